@@ -1,0 +1,471 @@
+/*
+ * oracle.c -- plain, slow FP64 reference of OpenFFT's 3-D C2C method.
+ *
+ * TEST INFRASTRUCTURE.  Only tests/, __graft_entry__.smoke() and the CPU
+ * baseline leg of bench.py load this library.  It shares no code, header,
+ * table or helper with the CUDA path in paper_1501_07350_gb300/, and the
+ * product path never loads it.
+ *
+ * What each part follows (Duy & Ozaki, "Performance Tuning of a Parallel 3-D
+ * FFT Package OpenFFT"):
+ *   - Eq. 1       row-major map of a 3-D point to a 1-D index;
+ *   - Eq. 2       the partition function f(N1,N2,N3,Np,myid);
+ *   - Eqs. 3-4    block distribution x^s = f(id), x^e = f(id+1)-1;
+ *   - Eqs. 5-7    translation of x^s / x^e back to 3-D coordinates;
+ *   - Eqs. 8-9    the 2-D (pencil) form taken when N1 < Np <= N1*N2;
+ *   - Sec. 2      transpose order abc -> cab -> cba;
+ *   - Sec. 3.1.1  execution: per rank copy a line out, 1-D FFT, copy back;
+ *                 pack a send buffer per destination, communicate, unpack
+ *                 and merge into the next decomposition.
+ *
+ * Readings where the paper is silent (each is listed in the design doc):
+ *   - stage s transforms the fastest axis of its ordering: c in abc, b in
+ *     cab, a in cba (each rank owns complete lines of that axis);
+ *   - the degree (1-D or 2-D) is chosen per ordering from its own leading
+ *     dimensions; Np > N1*N2 is undefined by Eq. 2 and is rejected;
+ *   - forward = exp(-2 pi i ...), unnormalised; backward = exp(+2 pi i ...)
+ *     with a final division by N, input in cba order, output in abc order,
+ *     axes transformed a, b, c;
+ *   - inside a send segment, elements are kept in ascending source index.
+ *
+ * Arithmetic: plain double, no compensated sums, so the FFT error grows like
+ * u*log(n).  Twiddles are evaluated in long double and rounded once.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+typedef struct { double re, im; } cplx;
+
+static const long double PI_L = 3.141592653589793238462643383279502884L;
+
+/* ---------------------------------------------------------------- Eq. 2 -- */
+
+/* Start offset of process `id` in the 1-D order of an (N1,N2,N3) ordering.
+ * Returns -1 where Eq. 2 is undefined (Np > N1*N2 or bad arguments). */
+int64_t oracle_f(int64_t N1, int64_t N2, int64_t N3, int64_t Np, int64_t id)
+{
+    if (N1 < 1 || N2 < 1 || N3 < 1 || Np < 1 || id < 0 || id > Np) return -1;
+    if (Np <= N1) return ((N1 * id) / Np) * N2 * N3;           /* 1-D slabs   */
+    if (Np <= N1 * N2) return ((N1 * N2 * id) / Np) * N3;      /* 2-D pencils */
+    return -1;
+}
+
+/* Eqs. 3-4 for all ranks: xs[id] = f(id) for id = 0..Np (so x^e = xs[id+1]-1). */
+int oracle_boundaries(int64_t N1, int64_t N2, int64_t N3, int64_t Np, int64_t* xs)
+{
+    for (int64_t id = 0; id <= Np; ++id) {
+        xs[id] = oracle_f(N1, N2, N3, Np, id);
+        if (xs[id] < 0) return -1;
+    }
+    return 0;
+}
+
+/* Eqs. 5-7: 1-D index -> (a,b,c) coordinates of the (N1,N2,N3) ordering. */
+void oracle_to3d(int64_t N1, int64_t N2, int64_t N3, int64_t x, int64_t abc[3])
+{
+    (void)N1;
+    int64_t a = x / (N2 * N3);
+    int64_t b = (x - a * N2 * N3) / N3;
+    int64_t c = x - a * N2 * N3 - b * N3;
+    abc[0] = a; abc[1] = b; abc[2] = c;
+}
+
+/* Box of rank `id`: x^s, x^e (Eqs. 3-4) and their 3-D coordinates (Eqs. 5-7). */
+int oracle_box(int64_t N1, int64_t N2, int64_t N3, int64_t Np, int64_t id,
+               int64_t* xs, int64_t* xe, int64_t start3[3], int64_t end3[3])
+{
+    int64_t s = oracle_f(N1, N2, N3, Np, id);
+    int64_t e = oracle_f(N1, N2, N3, Np, id + 1);
+    if (s < 0 || e < 0) return -1;
+    *xs = s;
+    *xe = e - 1;
+    oracle_to3d(N1, N2, N3, s, start3);
+    if (e - 1 >= s) oracle_to3d(N1, N2, N3, e - 1, end3);
+    else { end3[0] = end3[1] = end3[2] = -1; }   /* empty box */
+    return 0;
+}
+
+/* Degree of an ordering: 1 = slabs (Np <= N1), 2 = pencils, -1 undefined. */
+int oracle_degree(int64_t N1, int64_t N2, int64_t Np)
+{
+    if (Np <= N1) return 1;
+    if (Np <= N1 * N2) return 2;
+    return -1;
+}
+
+/* ------------------------------------------------------------ orderings -- */
+
+/* Layout codes: 0 = abc, 1 = cab, 2 = cba (slowest axis first).  axis[i] is
+ * the original axis (0=a, 1=b, 2=c) that is the i-th dimension of the layout. */
+static void layout_axes(int layout, int axis[3])
+{
+    static const int tab[3][3] = {{0, 1, 2}, {2, 0, 1}, {2, 1, 0}};
+    axis[0] = tab[layout][0]; axis[1] = tab[layout][1]; axis[2] = tab[layout][2];
+}
+
+static void layout_dims(int layout, const int64_t n[3], int64_t D[3])
+{
+    int axis[3];
+    layout_axes(layout, axis);
+    D[0] = n[axis[0]]; D[1] = n[axis[1]]; D[2] = n[axis[2]];
+}
+
+/* Eq. 1 applied to the layout: point (v[0]=a, v[1]=b, v[2]=c) -> 1-D index. */
+static int64_t layout_index(int layout, const int64_t n[3], const int64_t v[3])
+{
+    int axis[3]; int64_t D[3];
+    layout_axes(layout, axis);
+    layout_dims(layout, n, D);
+    return (v[axis[0]] * D[1] + v[axis[1]]) * D[2] + v[axis[2]];
+}
+
+/* 1-D index in the layout -> point (a,b,c), by Eqs. 5-7. */
+static void layout_point(int layout, const int64_t n[3], int64_t x, int64_t v[3])
+{
+    int axis[3]; int64_t D[3], d[3];
+    layout_axes(layout, axis);
+    layout_dims(layout, n, D);
+    oracle_to3d(D[0], D[1], D[2], x, d);
+    v[axis[0]] = d[0]; v[axis[1]] = d[1]; v[axis[2]] = d[2];
+}
+
+/* Owner of 1-D index y: the rank whose [x^s, x^e] holds it, by bisection over
+ * the ascending boundaries xs[0..Np]. */
+static int64_t owner_of(const int64_t* xs, int64_t Np, int64_t y)
+{
+    int64_t lo = 0, hi = Np - 1;           /* invariant: xs[lo] <= y < xs[hi+1] */
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) / 2;
+        if (xs[mid] <= y) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+/* ------------------------------------------------------- 1-D FFT engine -- */
+
+/* Table W[e] = exp(sign * 2 pi i e / n), e = 0..n-1, in long double, rounded. */
+static cplx* make_table(int64_t n, int sign)
+{
+    cplx* W = (cplx*)malloc(sizeof(cplx) * (size_t)n);
+    for (int64_t e = 0; e < n; ++e) {
+        long double ang = 2.0L * PI_L * (long double)e / (long double)n;
+        W[e].re = (double)cosl(ang);
+        W[e].im = (double)((long double)sign * sinl(ang));
+    }
+    return W;
+}
+
+static inline cplx cmul(cplx a, cplx b)
+{
+    cplx r;
+    r.re = a.re * b.re - a.im * b.im;
+    r.im = a.re * b.im + a.im * b.re;
+    return r;
+}
+
+static int is_prime(int64_t n)
+{
+    if (n < 2) return 0;
+    for (int64_t p = 2; p * p <= n; ++p) if (n % p == 0) return 0;
+    return 1;
+}
+
+/* Radix of one decimation-in-time split: 4, then 2, 3, 5, else the smallest
+ * prime factor; 0 means "take the direct DFT" (n <= 5 or n prime). */
+static int64_t choose_radix(int64_t n)
+{
+    if (n <= 5 || is_prime(n)) return 0;
+    if (n % 4 == 0) return 4;
+    if (n % 2 == 0) return 2;
+    if (n % 3 == 0) return 3;
+    if (n % 5 == 0) return 5;
+    for (int64_t p = 7; p <= n; ++p) if (n % p == 0) return p;
+    return 0;
+}
+
+/* y[0..n) = DFT_n of x[0], x[stride], ...; W is the table of length Wn, and
+ * W_n^e = W[e * (Wn / n)].  Recursive decimation in time:
+ *   X[k + q m] = sum_j W_r^{j q} (W_n^{j k} Y_j[k]),   n = r m,
+ * where Y_j is the m-point DFT of the subsequence x[j + r t]. */
+static void fft_rec(int64_t n, const cplx* x, int64_t stride, cplx* y,
+                    const cplx* W, int64_t Wn)
+{
+    int64_t step = Wn / n;
+    if (n == 1) { y[0] = x[0]; return; }
+    int64_t r = choose_radix(n);
+    if (r == 0) {                                      /* direct DFT */
+        for (int64_t k = 0; k < n; ++k) {
+            cplx acc = {0.0, 0.0};
+            for (int64_t j = 0; j < n; ++j) {
+                cplx t = cmul(x[j * stride], W[((j * k) % n) * step]);
+                acc.re += t.re; acc.im += t.im;
+            }
+            y[k] = acc;
+        }
+        return;
+    }
+    int64_t m = n / r;
+    for (int64_t j = 0; j < r; ++j)
+        fft_rec(m, x + j * stride, stride * r, y + j * m, W, Wn);
+    cplx* t = (cplx*)malloc(sizeof(cplx) * (size_t)(2 * r));
+    cplx* z = t + r;
+    for (int64_t k = 0; k < m; ++k) {
+        for (int64_t j = 0; j < r; ++j)
+            t[j] = cmul(y[j * m + k], W[((j * k) % n) * step]);
+        for (int64_t q = 0; q < r; ++q) {
+            cplx acc = {0.0, 0.0};
+            for (int64_t j = 0; j < r; ++j) {
+                /* W_r^{jq} = W_n^{jq m} */
+                cplx u = cmul(t[j], W[(((j * q) % r) * m) * step]);
+                acc.re += u.re; acc.im += u.im;
+            }
+            z[q] = acc;
+        }
+        for (int64_t q = 0; q < r; ++q) y[k + q * m] = z[q];
+    }
+    free(t);
+}
+
+/* Unnormalised 1-D DFT of length n with exponent sign `sign` (-1 forward). */
+void oracle_fft1d(int64_t n, const cplx* x, cplx* y, int sign)
+{
+    cplx* W = make_table(n, sign);
+    fft_rec(n, x, 1, y, W, n);
+    free(W);
+}
+
+/* Brute-force O(n^2) DFT, long double accumulation (pins oracle_fft1d). */
+void oracle_dft1d_brute(int64_t n, const cplx* x, cplx* y, int sign)
+{
+    for (int64_t k = 0; k < n; ++k) {
+        long double sr = 0.0L, si = 0.0L;
+        for (int64_t j = 0; j < n; ++j) {
+            long double ang = 2.0L * PI_L * (long double)((j * k) % n) / (long double)n;
+            long double c = cosl(ang), s = (long double)sign * sinl(ang);
+            sr += (long double)x[j].re * c - (long double)x[j].im * s;
+            si += (long double)x[j].re * s + (long double)x[j].im * c;
+        }
+        y[k].re = (double)sr; y[k].im = (double)si;
+    }
+}
+
+/* Brute-force O(N^2) 3-D DFT on A[a][b][c] (abc order), output X[ka][kb][kc]
+ * in the same order, long double accumulation.  Phase index is reduced
+ * exactly in integers: t = (a ka mod Na) N/Na + (b kb mod Nb) N/Nb + ... */
+void oracle_dft3d_brute(int64_t Na, int64_t Nb, int64_t Nc, const cplx* A, cplx* X, int sign)
+{
+    int64_t N = Na * Nb * Nc;
+    for (int64_t ka = 0; ka < Na; ++ka)
+    for (int64_t kb = 0; kb < Nb; ++kb)
+    for (int64_t kc = 0; kc < Nc; ++kc) {
+        long double sr = 0.0L, si = 0.0L;
+        for (int64_t a = 0; a < Na; ++a)
+        for (int64_t b = 0; b < Nb; ++b)
+        for (int64_t c = 0; c < Nc; ++c) {
+            int64_t t = ((a * ka) % Na) * (N / Na) + ((b * kb) % Nb) * (N / Nb)
+                      + ((c * kc) % Nc) * (N / Nc);
+            t %= N;
+            long double ang = 2.0L * PI_L * (long double)t / (long double)N;
+            long double cr = cosl(ang), ci = (long double)sign * sinl(ang);
+            const cplx v = A[(a * Nb + b) * Nc + c];
+            sr += (long double)v.re * cr - (long double)v.im * ci;
+            si += (long double)v.re * ci + (long double)v.im * cr;
+        }
+        X[(ka * Nb + kb) * Nc + kc].re = (double)sr;
+        X[(ka * Nb + kb) * Nc + kc].im = (double)si;
+    }
+}
+
+/* One output line of the 3-D DFT by its definition, summed axis by axis:
+ *   X[ka,kb,kc] = sum_a W_a^{a ka} sum_b W_b^{b kb} sum_c W_c^{c kc} A[a,b,c],
+ * for all ka at fixed (kb,kc).  O(N) work, used to sample full-size outputs. */
+void oracle_dft3d_line(int64_t Na, int64_t Nb, int64_t Nc, const cplx* A, int sign,
+                       int64_t kb, int64_t kc, cplx* line)
+{
+    cplx* Wa = make_table(Na, sign);
+    cplx* Wb = make_table(Nb, sign);
+    cplx* Wc = make_table(Nc, sign);
+    cplx* s = (cplx*)malloc(sizeof(cplx) * (size_t)Na);
+    for (int64_t a = 0; a < Na; ++a) {
+        cplx sb = {0.0, 0.0};
+        for (int64_t b = 0; b < Nb; ++b) {
+            cplx sc = {0.0, 0.0};
+            const cplx* row = A + (a * Nb + b) * Nc;
+            for (int64_t c = 0; c < Nc; ++c) {
+                cplx t = cmul(row[c], Wc[(c * kc) % Nc]);
+                sc.re += t.re; sc.im += t.im;
+            }
+            cplx t = cmul(sc, Wb[(b * kb) % Nb]);
+            sb.re += t.re; sb.im += t.im;
+        }
+        s[a] = sb;
+    }
+    for (int64_t ka = 0; ka < Na; ++ka) {
+        cplx acc = {0.0, 0.0};
+        for (int64_t a = 0; a < Na; ++a) {
+            cplx t = cmul(s[a], Wa[(a * ka) % Na]);
+            acc.re += t.re; acc.im += t.im;
+        }
+        line[ka] = acc;
+    }
+    free(Wa); free(Wb); free(Wc); free(s);
+}
+
+/* ------------------------------------------------- redistribution steps -- */
+
+/* Steps (4)-(6) of the execution flow for one transpose, literally:
+ * every source rank r packs, in ascending source index, the (destination
+ * index, value) pairs of its box into one segment per destination rank s;
+ * the segments are communicated (copied into the receive buffer of s, in
+ * order of source rank); every destination rank unpacks its receive buffer
+ * into its box of the next ordering.  C[r*Np+s] receives the element count
+ * of segment (r, s).  Returns 0, or -1 on an undefined decomposition / an
+ * element that would land outside the receiver's box. */
+static int redistribute(int src_layout, int dst_layout, const int64_t n[3], int64_t Np,
+                        const cplx* src, cplx* dst, int64_t* C)
+{
+    int64_t Ds[3], Dd[3];
+    layout_dims(src_layout, n, Ds);
+    layout_dims(dst_layout, n, Dd);
+    int64_t N = n[0] * n[1] * n[2];
+    int64_t* xs_src = (int64_t*)malloc(sizeof(int64_t) * (size_t)(Np + 1));
+    int64_t* xs_dst = (int64_t*)malloc(sizeof(int64_t) * (size_t)(Np + 1));
+    if (oracle_boundaries(Ds[0], Ds[1], Ds[2], Np, xs_src) ||
+        oracle_boundaries(Dd[0], Dd[1], Dd[2], Np, xs_dst)) {
+        free(xs_src); free(xs_dst);
+        return -1;
+    }
+    int64_t* cnt = (int64_t*)calloc((size_t)(Np * Np), sizeof(int64_t));
+    /* count: which destination each source element goes to */
+    for (int64_t r = 0; r < Np; ++r)
+        for (int64_t x = xs_src[r]; x < xs_src[r + 1]; ++x) {
+            int64_t v[3];
+            layout_point(src_layout, n, x, v);
+            int64_t y = layout_index(dst_layout, n, v);
+            cnt[r * Np + owner_of(xs_dst, Np, y)] += 1;
+        }
+    /* send displacements: rank r's send buffer spans [xs_src[r], xs_src[r+1]) */
+    int64_t* sdispl = (int64_t*)malloc(sizeof(int64_t) * (size_t)(Np * Np));
+    int64_t* rdispl = (int64_t*)malloc(sizeof(int64_t) * (size_t)(Np * Np));
+    for (int64_t r = 0; r < Np; ++r) {
+        int64_t off = xs_src[r];
+        for (int64_t s = 0; s < Np; ++s) { sdispl[r * Np + s] = off; off += cnt[r * Np + s]; }
+    }
+    /* receive displacements: rank s's receive buffer spans [xs_dst[s], xs_dst[s+1]) */
+    for (int64_t s = 0; s < Np; ++s) {
+        int64_t off = xs_dst[s];
+        for (int64_t r = 0; r < Np; ++r) { rdispl[s * Np + r] = off; off += cnt[r * Np + s]; }
+    }
+    /* (4) pack */
+    int64_t* sidx = (int64_t*)malloc(sizeof(int64_t) * (size_t)N);
+    cplx* sval = (cplx*)malloc(sizeof(cplx) * (size_t)N);
+    int64_t* fill = (int64_t*)calloc((size_t)(Np * Np), sizeof(int64_t));
+    for (int64_t r = 0; r < Np; ++r)
+        for (int64_t x = xs_src[r]; x < xs_src[r + 1]; ++x) {
+            int64_t v[3];
+            layout_point(src_layout, n, x, v);
+            int64_t y = layout_index(dst_layout, n, v);
+            int64_t s = owner_of(xs_dst, Np, y);
+            int64_t pos = sdispl[r * Np + s] + fill[r * Np + s]++;
+            sidx[pos] = y;
+            sval[pos] = src[x];
+        }
+    /* (5) communicate */
+    int64_t* ridx = (int64_t*)malloc(sizeof(int64_t) * (size_t)N);
+    cplx* rval = (cplx*)malloc(sizeof(cplx) * (size_t)N);
+    for (int64_t s = 0; s < Np; ++s)
+        for (int64_t r = 0; r < Np; ++r) {
+            int64_t len = cnt[r * Np + s];
+            memcpy(ridx + rdispl[s * Np + r], sidx + sdispl[r * Np + s], sizeof(int64_t) * (size_t)len);
+            memcpy(rval + rdispl[s * Np + r], sval + sdispl[r * Np + s], sizeof(cplx) * (size_t)len);
+        }
+    /* (6) unpack into the receiver's box */
+    int bad = 0;
+    for (int64_t s = 0; s < Np; ++s)
+        for (int64_t p = xs_dst[s]; p < xs_dst[s + 1]; ++p) {
+            int64_t y = ridx[p];
+            if (y < xs_dst[s] || y >= xs_dst[s + 1]) { bad = 1; continue; }
+            dst[y] = rval[p];
+        }
+    if (C) memcpy(C, cnt, sizeof(int64_t) * (size_t)(Np * Np));
+    free(xs_src); free(xs_dst); free(cnt); free(sdispl); free(rdispl);
+    free(sidx); free(sval); free(fill); free(ridx); free(rval);
+    return bad ? -1 : 0;
+}
+
+/* Transpose alone.  which: 1 = abc->cab, 2 = cab->cba, -2 = cba->cab,
+ * -1 = cab->abc.  C (Np*Np, may be NULL) receives the count matrix. */
+int oracle_redistribute(int64_t Na, int64_t Nb, int64_t Nc, int64_t Np, int which,
+                        const cplx* src, cplx* dst, int64_t* C)
+{
+    const int64_t n[3] = {Na, Nb, Nc};
+    switch (which) {
+    case 1:  return redistribute(0, 1, n, Np, src, dst, C);
+    case 2:  return redistribute(1, 2, n, Np, src, dst, C);
+    case -2: return redistribute(2, 1, n, Np, src, dst, C);
+    case -1: return redistribute(1, 0, n, Np, src, dst, C);
+    default: return -1;
+    }
+}
+
+/* Steps (1)-(3): every rank copies each complete line of the fastest axis of
+ * its box into a line buffer, transforms it, and copies it back. */
+static int transform_stage(int layout, const int64_t n[3], int64_t Np, cplx* data, int sign)
+{
+    int64_t D[3];
+    layout_dims(layout, n, D);
+    int64_t* xs = (int64_t*)malloc(sizeof(int64_t) * (size_t)(Np + 1));
+    if (oracle_boundaries(D[0], D[1], D[2], Np, xs)) { free(xs); return -1; }
+    int64_t len = D[2];
+    cplx* W = make_table(len, sign);
+    cplx* buf = (cplx*)malloc(sizeof(cplx) * (size_t)len);
+    cplx* res = (cplx*)malloc(sizeof(cplx) * (size_t)len);
+    for (int64_t r = 0; r < Np; ++r)
+        for (int64_t x = xs[r]; x < xs[r + 1]; x += len) {        /* box = whole lines */
+            memcpy(buf, data + x, sizeof(cplx) * (size_t)len);    /* (1) */
+            fft_rec(len, buf, 1, res, W, len);                    /* (2) */
+            memcpy(data + x, res, sizeof(cplx) * (size_t)len);    /* (3) */
+        }
+    free(W); free(buf); free(res); free(xs);
+    return 0;
+}
+
+/* Full 3-D C2C transform under the decomposition.
+ *   dir = -1 (forward): in = abc order, out = cba order; stages c, b, a.
+ *   dir = +1 (backward): in = cba order, out = abc order; stages a, b, c,
+ *                        then division by N.
+ * C1 / C2 (Np*Np each, may be NULL) receive the count matrices of the first
+ * and second transpose of this direction.  Returns 0 or -1. */
+int oracle_fft3d(int64_t Na, int64_t Nb, int64_t Nc, int64_t Np, int dir,
+                 const cplx* in, cplx* out, int64_t* C1, int64_t* C2)
+{
+    const int64_t n[3] = {Na, Nb, Nc};
+    int64_t N = Na * Nb * Nc;
+    if (dir != -1 && dir != 1) return -1;
+    cplx* t0 = (cplx*)malloc(sizeof(cplx) * (size_t)N);
+    cplx* t1 = (cplx*)malloc(sizeof(cplx) * (size_t)N);
+    memcpy(t0, in, sizeof(cplx) * (size_t)N);
+    int rc = 0;
+    if (dir == -1) {
+        rc |= transform_stage(0, n, Np, t0, -1);             /* along c in abc */
+        rc |= redistribute(0, 1, n, Np, t0, t1, C1);         /* abc -> cab     */
+        rc |= transform_stage(1, n, Np, t1, -1);             /* along b in cab */
+        rc |= redistribute(1, 2, n, Np, t1, t0, C2);         /* cab -> cba     */
+        rc |= transform_stage(2, n, Np, t0, -1);             /* along a in cba */
+        memcpy(out, t0, sizeof(cplx) * (size_t)N);
+    } else {
+        rc |= transform_stage(2, n, Np, t0, 1);              /* along a in cba */
+        rc |= redistribute(2, 1, n, Np, t0, t1, C1);         /* cba -> cab     */
+        rc |= transform_stage(1, n, Np, t1, 1);              /* along b in cab */
+        rc |= redistribute(1, 0, n, Np, t1, t0, C2);         /* cab -> abc     */
+        rc |= transform_stage(0, n, Np, t0, 1);              /* along c in abc */
+        for (int64_t i = 0; i < N; ++i) {
+            out[i].re = t0[i].re / (double)N;
+            out[i].im = t0[i].im / (double)N;
+        }
+    }
+    free(t0); free(t1);
+    return rc ? -1 : 0;
+}
