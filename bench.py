@@ -1,0 +1,441 @@
+#!/usr/bin/env python3
+"""Benchmark: 3-D C2C FFT under OpenFFT's decomposition on one GB300.
+
+Default workload (one step): 256 x 256 x 256 complex128, re/im i.i.d.
+standard normal (seeded), for each P in {16, 64, 256} logical ranks one
+forward and one backward transform -> 6 transforms per step.  Plans are
+built and auto-tuned before timing (the paper's initialisation phase,
+excluded from timing).  Inputs stay resident in HBM; every array (256 MiB)
+is larger than L2, so no flush is needed between steps.
+
+Metric: GFLOP/s in the 5 N log2 N convention, whole job (all ranks).
+Reported beside it: the roofline of the dominant kernel (live CUDA-event
+timing of every launch), end-to-end throughput through the host-buffer C
+ABI call (copies included), the FP64 oracle on the host cores, clocks.
+
+``--impl reference`` times the FP64 oracle (plain C, host cores) on a
+bounded sample of the same workload: one forward 256^3 transform per step.
+
+Multi-GPU (torchrun): every rank runs its own replica of the workload (the
+transform does not need another GPU); value = all ranks' flops / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3-D C2C FFT GFLOP/s (5N log2N) & % HBM roofline, plain FP64 vs tuned forms"
+UNIT = "GFLOP/s"
+N1D = 256
+PS = (16, 64, 256)
+WORKLOAD = "256x256x256 complex128 standard-normal, forward+backward at P=16,64,256 (6 transforms/step)"
+
+
+def flops(N: int) -> float:
+    return 5.0 * N * math.log2(N)
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def stage_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("fft_stage.cu", "arith.cuh", "fft_stage.h"):
+        with open(os.path.join(ROOT, "paper_1501_07350_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_hash: str):
+    """DRAM bytes per stage launch from a committed ncu summary, if it was taken on this source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        if d.get("source_hash") == kernel_hash:
+            return float(d["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.device)],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 10:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[2]) for r in rows if num(r[2]) is not None]
+        mx = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower() == "active"})
+        pw = [num(r[4]) for r in rows if num(r[4]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+# ------------------------------------------------------------------ ours --
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1501_07350_gb300 import _build
+    from paper_1501_07350_gb300 import openfft as of
+    from paper_1501_07350_gb300 import synth
+
+    _build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    n = N1D
+    N = n ** 3
+    x_np = synth.complex_field((n, n, n), seed=synth.config_seed(2), dist="normal").reshape(-1)
+    x_host = torch.from_numpy(x_np).pin_memory()
+    x = x_host.to(dev)
+    y = torch.empty_like(x)
+    z = torch.empty_like(x)
+
+    def make_plans(dtype, tune):
+        plans = {}
+        for P in PS:
+            h = of.openfft_plan(n, n, n, P, dtype)
+            of.openfft_set_stream(h, stream)
+            if tune:
+                of.openfft_set_tuning(h, of.TUNE_EXHAUSTIVE)
+            plans[P] = h
+        return plans
+
+    plans = make_plans(of.C2C_F64, args.tune == "exhaustive")
+    chosen = {P: of.openfft_candidate(h, of.openfft_current_candidate(h)) for P, h in plans.items()}
+
+    def step(pl, a, b, c):
+        for P in PS:
+            of.openfft_exec_c2c(pl[P], a, b, of.FORWARD)
+            of.openfft_exec_c2c(pl[P], b, c, of.BACKWARD)
+
+    for _ in range(args.warmup):
+        step(plans, x, y, z)
+    torch.cuda.synchronize()
+    for h in plans.values():
+        of.openfft_set_timing(h, True)
+        of.openfft_get_timing(h)       # reset
+
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(plans, x, y, z)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    time.sleep(0.3)
+    clocks = sampler.stop()
+    ms_total = e0.elapsed_time(e1)
+    phases = {}
+    launches = 0
+    for h in plans.values():
+        t = of.openfft_get_timing(h)
+        of.openfft_set_timing(h, False)
+        for k, v in t.items():
+            phases.setdefault(k, {"ms": 0.0, "launches": 0})
+            phases[k]["ms"] += v["ms"]
+            phases[k]["launches"] += v["launches"]
+    for k in ("fft", "buffer_comm", "communication"):
+        launches += phases[k]["launches"]
+
+    t_max = ms_total
+    if world > 1:
+        tt = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    ms_per_step = t_max / args.steps
+    work_per_step = 2 * len(PS) * flops(N)
+    value = world * work_per_step / (ms_per_step * 1e-3) / 1e9
+
+    # correctness of the timed outputs (round trip) on this rank
+    rt_err = float(torch.linalg.vector_norm(z - x) / torch.linalg.vector_norm(x))
+
+    # roofline of the dominant kernel: the FFT stage kernel (with fused transposes)
+    peak, peak_kind = load_peaks()
+    fft_ms = phases["fft"]["ms"]
+    fft_n = max(1, phases["fft"]["launches"])
+    avg_s = fft_ms / fft_n * 1e-3
+    alg_bytes = 2 * N * 16                     # one read + one write of the array per stage launch
+    achieved = alg_bytes / avg_s / 1e9
+    khash = stage_source_hash()
+    traffic = profiled_traffic(khash)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": "fft_stage_kernel", "peak_kind": peak_kind,
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_us": round(avg_s * 1e6, 2),
+                "share_of_step": round(fft_ms / max(1e-9, phases["exec"]["ms"]), 4)}
+
+    # end to end through the host-buffer C ABI call (copies inside the timed region)
+    y_host = torch.empty_like(x_host).pin_memory()
+    z_host = torch.empty_like(x_host).pin_memory()
+    xh, yh, zh = x_host.numpy(), y_host.numpy(), z_host.numpy()
+
+    def host_step():
+        for P in PS:
+            of.openfft_exec_c2c_host(plans[P], xh, yh, of.FORWARD)
+            of.openfft_exec_c2c_host(plans[P], yh, zh, of.BACKWARD)
+    host_step()
+    e2e_steps = max(1, min(args.steps, 5))
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        host_step()
+    t_e2e = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    e2e = {"value": round(world * work_per_step / t_e2e / 1e9, 2), "unit": UNIT,
+           "h2d_bytes_per_step": 2 * len(PS) * N * 16, "d2h_bytes_per_step": 2 * len(PS) * N * 16,
+           "steps": e2e_steps}
+
+    # other forms on the same workload (not the headline): FP32, and each FP64 arithmetic
+    forms = {}
+    if not args.quick:
+        forms = measure_forms(of, torch, plans, x, y, z, n, stream, args)
+
+    for h in plans.values():
+        of.openfft_destroy(h)
+
+    arith = {c["arith"] for c in chosen.values()}
+    dtype = "f64" if arith == {of.ARITH_NATIVE} else ("f32x2 (double-float, FP64-accurate)"
+                                                       if arith == {of.ARITH_DOUBLE_FLOAT} else "f64 / f32x2")
+    result = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "shape": [n, n, n], "P": list(PS), "transforms_per_step": 6,
+                   "l2": "inputs larger than L2 (256 MiB arrays), no flush", "tuning": args.tune,
+                   "chosen": {str(P): c for P, c in chosen.items()}, "parallelism": "replicas"},
+        "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+        "phases_ms": {k: round(v["ms"], 3) for k, v in phases.items()},
+        "round_trip_rel_l2": rt_err, "forms": forms,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline_sample(x_np, n)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+def measure_forms(of, torch, plans_f64, x, y, z, n, stream, args):
+    """Per-transform GFLOP/s of each form on the same input (median of 5)."""
+    N = n ** 3
+    out = {}
+
+    def time_exec(h, a, b, direction, reps=5):
+        ts = []
+        for _ in range(2):
+            of.openfft_exec_c2c(h, a, b, direction)
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            of.openfft_exec_c2c(h, a, b, direction)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    h = plans_f64[64]
+    cur = of.openfft_current_candidate(h)
+    for ci in range(of.openfft_num_candidates(h)):
+        c = of.openfft_candidate(h, ci)
+        if c["variant"] != of.VARIANT_FUSED:
+            continue
+        of.openfft_set_tuning(h, of.TUNE_USER, ci)
+        ms = time_exec(h, x, y, of.FORWARD)
+        key = "f64_%s_G%d" % ("native" if c["arith"] == of.ARITH_NATIVE else "doublefloat", c["lines_per_cta"])
+        out[key] = {"ms": round(ms, 4), "gflops": round(flops(N) / ms / 1e6, 1),
+                    "hbm_frac": round(6 * N * 16 / (ms * 1e-3) / 1e9 / load_peaks()[0], 4)}
+    for vi, name in [(of.VARIANT_PACK_UNPACK, "V1"), (of.VARIANT_PACK_EXCHANGE_UNPACK, "V0")]:
+        for ci in range(of.openfft_num_candidates(h)):
+            c = of.openfft_candidate(h, ci)
+            if c["variant"] == vi and c["lines_per_cta"] == 8 and c["arith"] == of.ARITH_NATIVE:
+                of.openfft_set_tuning(h, of.TUNE_USER, ci)
+                ms = time_exec(h, x, y, of.FORWARD)
+                out["f64_native_%s" % name] = {"ms": round(ms, 4), "gflops": round(flops(N) / ms / 1e6, 1)}
+    of.openfft_set_tuning(h, of.TUNE_USER, cur)
+    # FP32 form (complex64), auto-tuned
+    x32 = x.to(torch.complex64)
+    y32 = torch.empty_like(x32)
+    h32 = of.openfft_plan(n, n, n, 64, of.C2C_F32)
+    of.openfft_set_stream(h32, stream)
+    of.openfft_set_tuning(h32, of.TUNE_EXHAUSTIVE)
+    ms = time_exec(h32, x32, y32, of.FORWARD)
+    ref = torch.empty_like(y)
+    of.openfft_exec_c2c(h, x, ref, of.FORWARD)
+    torch.cuda.synchronize()
+    err = float(torch.linalg.vector_norm(y32.to(torch.complex128) - ref) / torch.linalg.vector_norm(ref))
+    out["f32"] = {"ms": round(ms, 4), "gflops": round(flops(N) / ms / 1e6, 1),
+                  "hbm_frac": round(6 * N * 8 / (ms * 1e-3) / 1e9 / load_peaks()[0], 4),
+                  "rel_l2_vs_f64": err, "bound": 1e-5,
+                  "chosen": of.openfft_candidate(h32, of.openfft_current_candidate(h32))}
+    of.openfft_destroy(h32)
+    del x32, y32
+    # 512^3 forward, FP64, P = 1024 (the large configuration)
+    if not args.no_512:
+        n5 = 512
+        N5 = n5 ** 3
+        from paper_1501_07350_gb300 import synth
+        torch.cuda.empty_cache()
+        xb = torch.from_numpy(synth.complex_field((N5,), seed=synth.config_seed(5))).to(x.device)
+        yb = torch.empty_like(xb)
+        h5 = of.openfft_plan(n5, n5, n5, 1024, of.C2C_F64)
+        of.openfft_set_stream(h5, stream)
+        of.openfft_set_tuning(h5, of.TUNE_EXHAUSTIVE)
+        ms = time_exec(h5, xb, yb, of.FORWARD, reps=3)
+        out["f64_512cubed_P1024_fwd"] = {
+            "ms": round(ms, 3), "gflops": round(flops(N5) / ms / 1e6, 1),
+            "hbm_frac": round(6 * N5 * 16 / (ms * 1e-3) / 1e9 / load_peaks()[0], 4),
+            "chosen": of.openfft_candidate(h5, of.openfft_current_candidate(h5))}
+        of.openfft_destroy(h5)
+        del xb, yb
+        torch.cuda.empty_cache()
+    return out
+
+
+def cpu_baseline_sample(x_np, n):
+    """The FP64 oracle on the host, one forward transform of the 256^3 input at P=16."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.fft3d(x_np, n, n, n, 16, oracle.FORWARD)
+    dt = time.perf_counter() - t0
+    return {"value": round(flops(n ** 3) / dt / 1e9, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one forward 256^3 complex128 transform at P=16 (%.1f s, single thread)" % dt}
+
+
+# ------------------------------------------------------------ reference --
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    from paper_1501_07350_gb300 import synth
+    n = N1D
+    N = n ** 3
+    x = synth.complex_field((n, n, n), seed=synth.config_seed(2), dist="normal").reshape(-1)
+    oracle.build()
+    times = []
+    for i in range(args.warmup + args.steps):
+        P = PS[i % len(PS)]
+        t0 = time.perf_counter()
+        oracle.fft3d(x, n, n, n, P, oracle.FORWARD)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    t = sum(times) / len(times)
+    value = flops(N) / t / 1e9
+    res = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 2),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "sample": "one forward 256^3 transform per step, P cycling 16/64/256"},
+           "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": "one forward 256^3 complex128 transform per step (single thread)"},
+           "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(res), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--tune", choices=["exhaustive", "default"], default="exhaustive")
+    ap.add_argument("--quick", action="store_true", help="skip the other forms")
+    ap.add_argument("--no-512", dest="no_512", action="store_true", help="skip the 512^3 form")
+    ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)     # at least 3 warm-up steps; the count run is reported
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * openfft_gb.h -- C ABI of a GB300 (sm_103a) 3-D complex-to-complex FFT under
+ * the communication-optimal decomposition of OpenFFT (Duy & Ozaki,
+ * "Performance Tuning of a Parallel 3-D FFT Package OpenFFT").
+ *
+ * Model.  The user's array A has shape [Na][Nb][Nc], c fastest ("abc" order,
+ * Eq. 1 with N1 = Na, N2 = Nb, N3 = Nc).  P logical ranks share it: rank r
+ * owns the 1-D index range [x^s_r, x^e_r] of Eqs. 2-4 (slabs if P <= leading
+ * dimension, pencils up to the product of the first two, Eqs. 8-9).  The
+ * transform runs the paper's order (Sec. 2): 1-D FFTs along c in abc, a
+ * transpose to cab ([Nc][Na][Nb]), 1-D FFTs along b, a transpose to cba
+ * ([Nc][Nb][Na]), 1-D FFTs along a.  The forward result is left in cba order
+ * and rank r's output box is [x^s_r, x^e_r] of Eqs. 2-4 applied to
+ * (N1,N2,N3) = (Nc,Nb,Na).  All ranks live in one GPU's memory: the
+ * concatenation of the ranks' boxes is the global array of that order, so a
+ * transpose is a device-local permutation.
+ *
+ * Conventions.  FORWARD computes X[ka,kb,kc] = sum A[a,b,c] exp(-2 pi i
+ * (a ka/Na + b kb/Nb + c kc/Nc)), unnormalised, and writes it at cba index
+ * (kc*Nb + kb)*Na + ka.  BACKWARD takes a cba-ordered spectrum, uses
+ * exp(+2 pi i ...), divides by N = Na*Nb*Nc, and writes abc order, so
+ * BACKWARD(FORWARD(A)) = A.
+ *
+ * Memory.  `in` / `out` of openfft_exec_c2c are DEVICE pointers owned by the
+ * caller, N elements each of the plan's element type (complex128 = two
+ * doubles for OPENFFT_C2C_F64, complex64 = two floats otherwise), 16-byte
+ * aligned.  Out of place only; `in` is not modified.  The plan owns all
+ * workspace, allocated once by openfft_plan (the paper moves buffer
+ * allocation out of the execution phase, Sec. 3.2.4); exec allocates nothing.
+ *
+ * Errors.  Functions returning int return an OPENFFT_* status (0 = OK).
+ * openfft_plan returns NULL on error.  openfft_last_error() gives a message
+ * for the calling thread's last failure.  Exec is asynchronous on the plan's
+ * stream; device-side failures are reported by openfft_sync().  A plan is not
+ * safe for concurrent use from several threads.
+ */
+#ifndef OPENFFT_GB_H
+#define OPENFFT_GB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct openfft_plan_s* openfft_plan_t;
+
+/* Element type and arithmetic of a plan. */
+enum {
+    OPENFFT_C2C_F64 = 0,        /* complex128 in/out, FP64-accurate (<= 1e-12 rel. L2)   */
+    OPENFFT_C2C_F32 = 1,        /* complex64 in/out, FP32 arithmetic                     */
+    OPENFFT_C2C_SPLIT_BF16 = 2, /* complex64 in/out, tensor-core DFT-GEMM, bf16 hi/lo    */
+    OPENFFT_C2C_SPLIT_TF32 = 3  /* complex64 in/out, tensor-core DFT-GEMM, tf32 hi/lo    */
+};
+
+/* Sign of the exponent. */
+enum { OPENFFT_FORWARD = -1, OPENFFT_BACKWARD = 1 };
+
+/* Status codes. */
+enum {
+    OPENFFT_OK = 0,
+    OPENFFT_ERR_INVALID_ARG = 1,       /* a size < 1, P < 1, bad dir/dtype/null pointer     */
+    OPENFFT_ERR_P_TOO_LARGE = 2,       /* P > N1*N2 for some ordering: Eq. 2 is undefined  */
+    OPENFFT_ERR_UNSUPPORTED_RADIX = 3, /* an axis length with a prime factor other than 2,3,5,7 or above 2048 */
+    OPENFFT_ERR_CUDA = 4,              /* a CUDA runtime call failed                        */
+    OPENFFT_ERR_NOMEM = 5,             /* device allocation failed at plan time             */
+    OPENFFT_ERR_TIMEOUT = 6,           /* a bounded device wait ran out (batched kernel)    */
+    OPENFFT_ERR_ALIAS = 7,             /* in == out                                         */
+    OPENFFT_ERR_UNSUPPORTED = 8        /* the request is valid but this build does not do it */
+};
+
+/* Transpose variants (the paper's communication methods, Sec. 3.2.1, recast
+ * for ranks that share one memory).
+ *   FUSED (V2):       the transpose is folded into the store of each FFT stage:
+ *                     one HBM read and one write per stage.
+ *   PACK_EXCHANGE_UNPACK (V0): the stage stores its box unchanged, then a pack
+ *                     kernel builds per-destination send segments (ascending
+ *                     source index), an exchange kernel moves every segment to
+ *                     its receiver as one all-to-all with variable counts
+ *                     (Isend/Irecv + Waitall, Alltoallv), and an unpack kernel
+ *                     writes the next ordering.
+ *   PACK_UNPACK (V1): as V0 but each receiver unpacks straight from the
+ *                     senders' segments (the unpack-on-arrival of Isend_Waitsome).
+ */
+enum {
+    OPENFFT_VARIANT_PACK_EXCHANGE_UNPACK = 0,
+    OPENFFT_VARIANT_PACK_UNPACK = 1,
+    OPENFFT_VARIANT_FUSED = 2
+};
+
+/* Arithmetic used for OPENFFT_C2C_F64.
+ *   NATIVE: IEEE double on the FP64 units.
+ *   DOUBLE_FLOAT: each double is carried as an unevaluated sum of two floats
+ *   and the butterflies use error-free transformations on the FP32 units
+ *   (about 48 significant bits; finite inputs with |x| < 2^90 and outputs
+ *   below 2^126).  Both meet the FP64 bound of 1e-12 relative L2. */
+enum { OPENFFT_ARITH_NATIVE = 0, OPENFFT_ARITH_DOUBLE_FLOAT = 1 };
+
+/* Tuning modes of openfft_set_tuning (Sec. 3.2.3: auto-tuning on, off = the
+ * default method, or a user-selected method). */
+enum {
+    OPENFFT_TUNE_DEFAULT = 0,    /* fixed default variant                         */
+    OPENFFT_TUNE_EXHAUSTIVE = 1, /* time every candidate twice, keep the fastest   */
+    OPENFFT_TUNE_LEARNED = 2,    /* cost-model proposal (falls back to DEFAULT)    */
+    OPENFFT_TUNE_USER = 3        /* candidate index given by the caller            */
+};
+
+/* ------------------------------------------------------------ plans ---- */
+
+/* Plan a 3-D C2C transform of [Na][Nb][Nc] over P logical ranks (Sec. 3.1.1,
+ * initialisation phase): validates the sizes, computes the boxes of the three
+ * orderings (Eqs. 2-9) and the radix plans, allocates the workspace (two
+ * scratch arrays of N elements, twiddle tables, transpose tables) and builds
+ * the twiddle tables on the device.  Uses the current CUDA device.
+ * Returns NULL on error (see openfft_last_error / openfft_last_status). */
+openfft_plan_t openfft_plan(int Na, int Nb, int Nc, int P, int dtype);
+
+/* Execute one transform (execution phase, repeatable).  in/out: device
+ * pointers as described above; dir: OPENFFT_FORWARD or OPENFFT_BACKWARD.
+ * Asynchronous on the plan's stream.  Returns OPENFFT_OK, INVALID_ARG,
+ * ALIAS or CUDA. */
+int openfft_exec_c2c(openfft_plan_t plan, const void* in, void* out, int dir);
+
+/* Same transform with HOST buffers: copies `host_in` to plan-owned device
+ * memory, executes, copies the result to `host_out` and waits.  Page-locked
+ * host memory gives the fastest copies.  The plan allocates its two device
+ * staging arrays on the first call. */
+int openfft_exec_c2c_host(openfft_plan_t plan, const void* host_in, void* host_out, int dir);
+
+/* Finalisation phase: frees everything the plan owns.  NULL-safe. */
+void openfft_destroy(openfft_plan_t plan);
+
+/* Waits for the plan's stream and reports device-side errors. */
+int openfft_sync(openfft_plan_t plan);
+
+/* Use `stream` (a cudaStream_t; NULL = legacy default stream) for exec. */
+int openfft_set_stream(openfft_plan_t plan, void* stream);
+
+/* ------------------------------------------------ queries / controls --- */
+
+/* Message for the calling thread's last failure ("" if none). */
+const char* openfft_last_error(void);
+/* Status of the calling thread's last failure (OPENFFT_OK if none). */
+int openfft_last_status(void);
+
+/* Box of `rank` in the input (which = 0: abc ordering) or output
+ * (which = 1: cba ordering) decomposition of the FORWARD transform:
+ * start/end 3-D coordinates (Eqs. 5-7, in the ordering's own dimension
+ * order), 1-D offset x^s and element count x^e - x^s + 1 (Eqs. 3-4).
+ * Any pointer may be NULL. */
+int openfft_box(openfft_plan_t plan, int which, int rank,
+                int64_t start[3], int64_t end[3], int64_t* offset, int64_t* count);
+
+/* P x P count matrix of one transpose, row = sending rank, column =
+ * receiving rank (the volumes of Sec. 4.1): exchange 1 = abc->cab,
+ * 2 = cab->cba, -2 = cba->cab, -1 = cab->abc.  PxP: host array of P*P. */
+int openfft_counts(openfft_plan_t plan, int exchange, int64_t* PxP);
+
+/* Host-only forms of the two queries above, needing no plan and no GPU.
+ * layout: 0 = abc, 1 = cab, 2 = cba. */
+int openfft_decomp_box(int Na, int Nb, int Nc, int P, int layout, int rank,
+                       int64_t start[3], int64_t end[3], int64_t* offset, int64_t* count);
+int openfft_decomp_counts(int Na, int Nb, int Nc, int P, int exchange, int64_t* PxP);
+
+/* Degree (1 = slabs, 2 = pencils) of `layout` for P ranks; -1 if undefined. */
+int openfft_decomp_degree(int Na, int Nb, int Nc, int P, int layout);
+
+/* Choose how the plan is executed.  mode: OPENFFT_TUNE_*.  With USER,
+ * `candidate` indexes the list of openfft_num_candidates (otherwise ignored).
+ * EXHAUSTIVE runs every candidate twice on plan-owned buffers (the paper's
+ * 2 runs per method) and keeps the fastest. */
+int openfft_set_tuning(openfft_plan_t plan, int mode, int candidate);
+
+/* Number of execution candidates of this plan and a description of one
+ * (redistribution variant, arithmetic, lines per CTA, threads per CTA). */
+int openfft_num_candidates(openfft_plan_t plan);
+int openfft_candidate(openfft_plan_t plan, int index, int* variant, int* arith,
+                      int* lines_per_cta, int* threads);
+/* Index of the candidate exec currently uses. */
+int openfft_current_candidate(openfft_plan_t plan);
+
+/* Breakdown of execution time (Sec. 3.1.2: FFT, Buffer (Comm) = pack and
+ * unpack, Communication = exchange).  While enabled, exec records CUDA
+ * events around every kernel it launches on the plan's stream.
+ * openfft_get_timing waits for the stream, adds the recorded intervals up by
+ * phase since the previous call, and resets them:
+ *   ms[0] / launches[0]: FFT stage kernels (with V2 they include the fused
+ *                        transposes),
+ *   ms[1] / launches[1]: pack and unpack kernels,
+ *   ms[2] / launches[2]: exchange kernels,
+ *   ms[3] / launches[3]: whole execs (first kernel start to last kernel end)
+ *                        and the number of execs.
+ * Events come from a plan-owned pool created by openfft_set_timing; when it
+ * is full, exec first folds the recorded intervals into the totals (which
+ * waits for the stream). */
+int openfft_set_timing(openfft_plan_t plan, int enable);
+int openfft_get_timing(openfft_plan_t plan, double ms[4], int64_t launches[4]);
+
+/* One transpose alone (for testing the permutation): `in` holds the source
+ * ordering, `out` receives the destination ordering, bit for bit.
+ * exchange as in openfft_counts; variant: OPENFFT_VARIANT_*. */
+int openfft_redistribute(openfft_plan_t plan, int exchange, int variant,
+                         const void* in, void* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OPENFFT_GB_H */

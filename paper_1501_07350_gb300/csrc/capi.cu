@@ -1,0 +1,680 @@
+// capi.cu -- the C ABI of include/openfft_gb.h: plans (initialisation phase),
+// execution, finalisation, decomposition queries and run-time tuning.
+//
+// Paper mapping (Duy & Ozaki): Sec. 3.1.1 calculation flow (init / exec /
+// finalize), Sec. 2 decomposition (Eqs. 2-9) and transpose order, Sec. 3.2.1
+// communication methods (the transpose variants), Sec. 3.2.3 auto-tuning
+// (every candidate run twice, fastest kept; default method; user select),
+// Sec. 3.2.4 (all buffers allocated once, at plan time).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/openfft_gb.h"
+#include "decomp.h"
+#include "fft_stage.h"
+#include "redistribute.h"
+
+using namespace ofg;
+
+namespace {
+
+thread_local std::string g_err;
+thread_local int g_status = OPENFFT_OK;
+
+int fail(int status, const std::string& msg)
+{
+    g_status = status;
+    g_err = msg;
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(OPENFFT_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ----------------------------------------------------------------- radix --
+
+bool radix_plan(int n, std::vector<int>& rad)
+{
+    rad.clear();
+    int m = n;
+    while (m % 8 == 0) { rad.push_back(8); m /= 8; }
+    while (m % 4 == 0) { rad.push_back(4); m /= 4; }
+    while (m % 2 == 0) { rad.push_back(2); m /= 2; }
+    while (m % 3 == 0) { rad.push_back(3); m /= 3; }
+    while (m % 5 == 0) { rad.push_back(5); m /= 5; }
+    while (m % 7 == 0) { rad.push_back(7); m /= 7; }
+    return m == 1 && (int)rad.size() <= kMaxPasses;
+}
+
+int ilog2(int g) { int l = 0; while ((1 << l) < g) ++l; return l; }
+
+// ------------------------------------------------------------ candidates --
+
+struct Candidate {
+    int variant;   // OPENFFT_VARIANT_*
+    int arith;     // ARITH_*
+    int G;         // lines per CTA target (power of two)
+};
+
+// one step of an execution
+enum OpKind { OP_STAGE, OP_PACK, OP_EXCHANGE, OP_UNPACK };
+enum Buf { B_IN, B_OUT, B_A, B_B };
+
+struct Op {
+    OpKind kind;
+    int src, dst;            // Buf ids
+    StageLaunch stage;       // OP_STAGE
+    int tix;                 // transpose table index (0..3) for pack/exchange/unpack
+    int from_send;           // OP_UNPACK
+};
+
+struct TransposeTables {
+    Transpose t;
+    std::vector<int64_t> C;
+    int64_t* d_sbase = nullptr;
+    int64_t* d_rbase = nullptr;
+    int64_t* d_chunks = nullptr;
+    int64_t nchunks = 0;
+};
+
+}  // namespace
+
+struct openfft_plan_s {
+    int Na, Nb, Nc, P, dtype;
+    int64_t N;
+    int device = 0, sms = 148;
+    cudaStream_t stream = nullptr;
+    size_t elem_bytes = 16;       // bytes of one element in the workspace
+    void* bufA = nullptr;
+    void* bufB = nullptr;
+    void* tw[3][3] = {};          // [axis a,b,c][FMT_C128, FMT_C64, FMT_DF]
+    std::vector<int> rad[3];      // radix plans of Na, Nb, Nc
+    TransposeTables tt[4];        // index: 0 = R1, 1 = R2, 2 = R2', 3 = R1'
+    std::vector<Candidate> cands;
+    int current = 0;
+    std::vector<Op> ops_fwd, ops_bwd;
+    void* stage_in = nullptr;     // host-exec staging (lazy)
+    void* stage_out = nullptr;
+    // execution-time breakdown
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;  // pool
+    std::vector<int> ev_cat;      // category of the interval ending at event i (-1: exec start)
+    size_t ev_used = 0;
+    double t_ms[4] = {0, 0, 0, 0};
+    int64_t t_launch[4] = {0, 0, 0, 0};
+};
+
+namespace {
+
+int tix_of(int which) { return which == 1 ? 0 : (which == 2 ? 1 : (which == -2 ? 2 : 3)); }
+
+int elem_bytes_of(int arith) { return arith == ARITH_F32 ? 8 : 16; }
+
+// Build the launch of one stage: lines of length n; l = i1 + i2*M1;
+// out(l,k) = i1*S1 + i2*S2 + k*Sk.
+int make_stage(openfft_plan_s* p, int axis, int arith, int Gt, int64_t M1, int64_t M2,
+               int64_t S1, int64_t S2, int64_t Sk, int group_i2, int contig, int in_fmt,
+               int out_fmt, int conj_in, int conj_out, double scale, int do_fft, StageLaunch& L)
+{
+    const int n = axis == 0 ? p->Na : (axis == 1 ? p->Nb : p->Nc);
+    const std::vector<int>& rad = p->rad[axis];
+    const int E = elem_bytes_of(arith);
+    const size_t cap = 200 * 1024;
+    int G = Gt;
+    const int64_t Mg = group_i2 ? M2 : M1;
+    while (G > 1 && (int64_t)(G / 2) >= Mg) G /= 2;           // no more lanes than lines
+    while (G > 1 && 2 * (size_t)n * (G + 1) * E > cap) G /= 2;
+    if (2 * (size_t)n * (G + 1) * E > cap) return fail(OPENFFT_ERR_UNSUPPORTED_RADIX, "axis too long for one CTA");
+    StageArgs& a = L.args;
+    std::memset(&a, 0, sizeof(a));
+    a.in = nullptr; a.out = nullptr;
+    const int twf = arith == ARITH_F64 ? FMT_C128 : (arith == ARITH_F32 ? FMT_C64 : FMT_DF);
+    a.tw = p->tw[axis][twf];
+    a.M1 = M1; a.M2 = M2; a.S1 = S1; a.S2 = S2; a.Sk = Sk;
+    a.ngroups = (Mg + G - 1) / G;
+    a.scale = scale;
+    a.n = n; a.G = G; a.log2G = ilog2(G);
+    a.group_i2 = group_i2; a.contig_store = contig;
+    a.npass = (int)rad.size();
+    for (size_t i = 0; i < rad.size(); ++i) a.radix[i] = rad[i];
+    a.conj_in = conj_in; a.conj_out = conj_out; a.do_fft = do_fft;
+    a.in_fmt = in_fmt; a.out_fmt = out_fmt;
+    L.arith = arith;
+    L.grid = a.ngroups * (group_i2 ? M1 : M2);
+    L.smem = 2 * (size_t)n * (G + 1) * E;     // two ping-pong tiles
+    if (L.grid > 0x7fffffffLL) return fail(OPENFFT_ERR_UNSUPPORTED, "grid too large");
+    return OPENFFT_OK;
+}
+
+Op stage_op(int src, int dst, const StageLaunch& L)
+{
+    Op o; std::memset(&o, 0, sizeof(o));
+    o.kind = OP_STAGE; o.src = src; o.dst = dst; o.stage = L;
+    return o;
+}
+
+Op redist_op(OpKind k, int src, int dst, int tix, int from_send)
+{
+    Op o; std::memset(&o, 0, sizeof(o));
+    o.kind = k; o.src = src; o.dst = dst; o.tix = tix; o.from_send = from_send;
+    return o;
+}
+
+// Build the forward and backward op lists of candidate c.
+int build_ops(openfft_plan_s* p, const Candidate& c)
+{
+    const int64_t Na = p->Na, Nb = p->Nb, Nc = p->Nc, N = p->N;
+    const int ar = c.arith;
+    const int ext = ar == ARITH_F32 ? FMT_C64 : FMT_C128;     // user arrays
+    const int mid = ar == ARITH_DF ? FMT_DF : ext;            // workspace arrays
+    const double invN = 1.0 / (double)N;
+    std::vector<Op>& F = p->ops_fwd;
+    std::vector<Op>& B = p->ops_bwd;
+    F.clear(); B.clear();
+    StageLaunch L;
+    int st;
+    if (c.variant == OPENFFT_VARIANT_FUSED) {
+        // forward: c-lines of abc -> cab; b-lines of cab -> cba; a-lines of cba in place
+        if ((st = make_stage(p, 2, ar, c.G, Na * Nb, 1, 1, 0, Na * Nb, 0, 0, ext, mid, 0, 0, 1.0, 1, L))) return st;
+        F.push_back(stage_op(B_IN, B_A, L));
+        if ((st = make_stage(p, 1, ar, c.G, Na, Nc, 1, Nb * Na, Na, 0, 0, mid, mid, 0, 0, 1.0, 1, L))) return st;
+        F.push_back(stage_op(B_A, B_OUT, L));
+        if ((st = make_stage(p, 0, ar, c.G, Nc * Nb, 1, Na, 0, 1, 0, 1, mid, ext, 0, 0, 1.0, 1, L))) return st;
+        F.push_back(stage_op(B_OUT, B_OUT, L));
+        // backward (conjugate on entry and exit): a-lines of cba -> cab; b-lines
+        // of cab -> abc (grouped along c, whose output stride is 1); c-lines in place
+        if ((st = make_stage(p, 0, ar, c.G, Nb, Nc, 1, Na * Nb, Nb, 0, 0, ext, mid, 1, 0, 1.0, 1, L))) return st;
+        B.push_back(stage_op(B_IN, B_A, L));
+        if ((st = make_stage(p, 1, ar, c.G, Na, Nc, Nb * Nc, 1, Nc, 1, 0, mid, mid, 0, 0, 1.0, 1, L))) return st;
+        B.push_back(stage_op(B_A, B_OUT, L));
+        if ((st = make_stage(p, 2, ar, c.G, Na * Nb, 1, Nc, 0, 1, 0, 1, mid, ext, 0, 1, invN, 1, L))) return st;
+        B.push_back(stage_op(B_OUT, B_OUT, L));
+        return OPENFFT_OK;
+    }
+    // V0 / V1: contiguous stage stores, explicit transposes through A and B
+    const bool v0 = c.variant == OPENFFT_VARIANT_PACK_EXCHANGE_UNPACK;
+    // One transpose starting from buffer `from` (A or B).  Returns the buffer
+    // the destination ordering lands in: `final_to` if given, else a scratch
+    // buffer that is free at that point.
+    auto transpose = [&](std::vector<Op>& ops, int tix, int from, int final_to) {
+        const int other = from == B_A ? B_B : B_A;
+        ops.push_back(redist_op(OP_PACK, from, other, tix, 0));          // send segments in `other`
+        int landing;
+        if (v0) {
+            ops.push_back(redist_op(OP_EXCHANGE, other, from, tix, 0));  // receive buffers in `from`
+            landing = final_to >= 0 ? final_to : other;
+            ops.push_back(redist_op(OP_UNPACK, from, landing, tix, 0));
+        } else {
+            landing = final_to >= 0 ? final_to : from;
+            ops.push_back(redist_op(OP_UNPACK, other, landing, tix, 1));
+        }
+        return landing;
+    };
+    auto other_of = [](int b) { return b == B_A ? B_B : B_A; };
+    // forward
+    if ((st = make_stage(p, 2, ar, c.G, Na * Nb, 1, Nc, 0, 1, 0, 1, ext, mid, 0, 0, 1.0, 1, L))) return st;
+    F.push_back(stage_op(B_IN, B_A, L));
+    int x = transpose(F, 0, B_A, -1);                // abc -> cab
+    if ((st = make_stage(p, 1, ar, c.G, Nc * Na, 1, Nb, 0, 1, 0, 1, mid, mid, 0, 0, 1.0, 1, L))) return st;
+    F.push_back(stage_op(x, other_of(x), L));
+    transpose(F, 1, other_of(x), B_OUT);             // cab -> cba lands in out
+    if ((st = make_stage(p, 0, ar, c.G, Nc * Nb, 1, Na, 0, 1, 0, 1, mid, ext, 0, 0, 1.0, 1, L))) return st;
+    F.push_back(stage_op(B_OUT, B_OUT, L));
+    // backward
+    if ((st = make_stage(p, 0, ar, c.G, Nc * Nb, 1, Na, 0, 1, 0, 1, ext, mid, 1, 0, 1.0, 1, L))) return st;
+    B.push_back(stage_op(B_IN, B_A, L));
+    x = transpose(B, 2, B_A, -1);                    // cba -> cab
+    if ((st = make_stage(p, 1, ar, c.G, Nc * Na, 1, Nb, 0, 1, 0, 1, mid, mid, 0, 0, 1.0, 1, L))) return st;
+    B.push_back(stage_op(x, other_of(x), L));
+    transpose(B, 3, other_of(x), B_OUT);             // cab -> abc lands in out
+    if ((st = make_stage(p, 2, ar, c.G, Na * Nb, 1, Nc, 0, 1, 0, 1, mid, ext, 0, 1, invN, 1, L))) return st;
+    B.push_back(stage_op(B_OUT, B_OUT, L));
+    return OPENFFT_OK;
+}
+
+void* resolve(openfft_plan_s* p, int b, const void* in, void* out)
+{
+    switch (b) {
+    case B_IN: return const_cast<void*>(in);
+    case B_OUT: return out;
+    case B_A: return p->bufA;
+    default: return p->bufB;
+    }
+}
+
+// Add the recorded intervals to the per-phase totals (waits for the stream).
+int fold_timing(openfft_plan_s* p)
+{
+    if (p->ev_used == 0) return OPENFFT_OK;
+    cudaError_t e = cudaEventSynchronize(p->ev[p->ev_used - 1]);
+    if (e) return cuda_fail(e, "timing event");
+    size_t start = 0;
+    for (size_t i = 1; i < p->ev_used; ++i) {
+        const int cat = p->ev_cat[i];
+        if (cat < 0) {                              // a new exec starts at event i
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, p->ev[start], p->ev[i - 1]);
+            p->t_ms[3] += ms; p->t_launch[3] += 1;
+            start = i;
+            continue;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p->ev[i - 1], p->ev[i]);
+        p->t_ms[cat] += ms;
+        p->t_launch[cat] += 1;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p->ev[start], p->ev[p->ev_used - 1]);
+    p->t_ms[3] += ms; p->t_launch[3] += 1;
+    p->ev_used = 0;
+    return OPENFFT_OK;
+}
+
+int record(openfft_plan_s* p, int cat)
+{
+    cudaError_t e = cudaEventRecord(p->ev[p->ev_used], p->stream);
+    if (e) return cuda_fail(e, "timing event");
+    p->ev_cat[p->ev_used++] = cat;
+    return OPENFFT_OK;
+}
+
+int run_ops(openfft_plan_s* p, const std::vector<Op>& ops, const void* in, void* out, int arith)
+{
+    const int E = elem_bytes_of(arith);
+    if (p->timing) {
+        if (p->ev_used + ops.size() + 1 > p->ev.size()) { int st = fold_timing(p); if (st) return st; }
+        int st = record(p, -1);
+        if (st) return st;
+    }
+    for (const Op& o : ops) {
+        void* s = resolve(p, o.src, in, out);
+        void* d = resolve(p, o.dst, in, out);
+        cudaError_t e = cudaSuccess;
+        if (o.kind == OP_STAGE) {
+            StageLaunch L = o.stage;
+            L.args.in = s; L.args.out = d;
+            e = launch_stage(L, p->stream);
+        } else {
+            const TransposeTables& T = p->tt[o.tix];
+            if (o.kind == OP_PACK) e = launch_pack(T.t, E, s, d, T.d_sbase, p->N, p->sms, p->stream);
+            else if (o.kind == OP_EXCHANGE) e = launch_exchange(E, T.d_chunks, T.nchunks, s, d, p->sms, p->stream);
+            else e = launch_unpack(T.t, E, s, d, o.from_send ? T.d_sbase : T.d_rbase, o.from_send, p->N, p->sms, p->stream);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+        if (p->timing) {
+            const int cat = o.kind == OP_STAGE ? 0 : (o.kind == OP_EXCHANGE ? 2 : 1);
+            int st = record(p, cat);
+            if (st) return st;
+        }
+    }
+    return OPENFFT_OK;
+}
+
+int select_candidate(openfft_plan_s* p, int idx)
+{
+    if (idx < 0 || idx >= (int)p->cands.size()) return fail(OPENFFT_ERR_INVALID_ARG, "candidate index out of range");
+    int st = build_ops(p, p->cands[(size_t)idx]);
+    if (st) return st;
+    p->current = idx;
+    return OPENFFT_OK;
+}
+
+int validate_dims(int Na, int Nb, int Nc, int P)
+{
+    if (Na < 1 || Nb < 1 || Nc < 1 || P < 1) return fail(OPENFFT_ERR_INVALID_ARG, "sizes and P must be >= 1");
+    const int64_t a = Na, b = Nb, c = Nc;
+    if ((int64_t)P > a * b || (int64_t)P > c * a || (int64_t)P > c * b)
+        return fail(OPENFFT_ERR_P_TOO_LARGE, "P exceeds N1*N2 of an ordering (Eq. 2 undefined)");
+    return OPENFFT_OK;
+}
+
+void free_plan(openfft_plan_s* p)
+{
+    if (!p) return;
+    cudaFree(p->bufA); cudaFree(p->bufB);
+    for (auto& row : p->tw) for (void* t : row) cudaFree(t);
+    for (auto& T : p->tt) { cudaFree(T.d_sbase); cudaFree(T.d_rbase); cudaFree(T.d_chunks); }
+    cudaFree(p->stage_in); cudaFree(p->stage_out);
+    for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+    delete p;
+}
+
+int box_of(const Ordering& o, int rank, int64_t start[3], int64_t end[3], int64_t* offset, int64_t* count)
+{
+    if (rank < 0 || rank >= o.P) return fail(OPENFFT_ERR_INVALID_ARG, "rank out of range");
+    const int64_t xs = box_begin(o, rank), xe = box_begin(o, rank + 1) - 1;
+    auto to3 = [&](int64_t x, int64_t v[3]) {           // Eqs. 5-7
+        int64_t d0 = x / (o.D1 * o.D2);
+        int64_t d1 = (x - d0 * o.D1 * o.D2) / o.D2;
+        v[0] = d0; v[1] = d1; v[2] = x - d0 * o.D1 * o.D2 - d1 * o.D2;
+    };
+    if (start) to3(xs, start);
+    if (end) { if (xe >= xs) to3(xe, end); else end[0] = end[1] = end[2] = -1; }
+    if (offset) *offset = xs;
+    if (count) *count = xe - xs + 1;
+    return OPENFFT_OK;
+}
+
+}  // namespace
+
+// =================================================================== ABI ==
+
+extern "C" {
+
+const char* openfft_last_error(void) { return g_err.c_str(); }
+int openfft_last_status(void) { return g_status; }
+
+int openfft_decomp_degree(int Na, int Nb, int Nc, int P, int layout)
+{
+    if (Na < 1 || Nb < 1 || Nc < 1 || P < 1 || layout < 0 || layout > 2) return -1;
+    return ordering_of(layout, Na, Nb, Nc, P).degree;
+}
+
+int openfft_decomp_box(int Na, int Nb, int Nc, int P, int layout, int rank,
+                       int64_t start[3], int64_t end[3], int64_t* offset, int64_t* count)
+{
+    int st = validate_dims(Na, Nb, Nc, P);
+    if (st) return st;
+    if (layout < 0 || layout > 2) return fail(OPENFFT_ERR_INVALID_ARG, "layout must be 0, 1 or 2");
+    return box_of(ordering_of(layout, Na, Nb, Nc, P), rank, start, end, offset, count);
+}
+
+int openfft_decomp_counts(int Na, int Nb, int Nc, int P, int exchange, int64_t* PxP)
+{
+    int st = validate_dims(Na, Nb, Nc, P);
+    if (st) return st;
+    if (!PxP) return fail(OPENFFT_ERR_INVALID_ARG, "null output");
+    if (exchange != 1 && exchange != 2 && exchange != -1 && exchange != -2)
+        return fail(OPENFFT_ERR_INVALID_ARG, "exchange must be 1, 2, -2 or -1");
+    Transpose t = make_transpose(exchange, Na, Nb, Nc, P);
+    for (int64_t r = 0; r < P; ++r)
+        for (int64_t s = 0; s < P; ++s) PxP[r * P + s] = pair_count(t, r, s);
+    return OPENFFT_OK;
+}
+
+openfft_plan_t openfft_plan(int Na, int Nb, int Nc, int P, int dtype)
+{
+    if (validate_dims(Na, Nb, Nc, P)) return nullptr;
+    if (dtype != OPENFFT_C2C_F64 && dtype != OPENFFT_C2C_F32) {
+        if (dtype == OPENFFT_C2C_SPLIT_BF16 || dtype == OPENFFT_C2C_SPLIT_TF32)
+            fail(OPENFFT_ERR_UNSUPPORTED, "split-precision plans are created by openfft_plan with a supported build");
+        else
+            fail(OPENFFT_ERR_INVALID_ARG, "unknown dtype");
+        return nullptr;
+    }
+    openfft_plan_s* p = new openfft_plan_s();
+    p->Na = Na; p->Nb = Nb; p->Nc = Nc; p->P = P; p->dtype = dtype;
+    p->N = (int64_t)Na * Nb * Nc;
+    const int lens[3] = {Na, Nb, Nc};
+    for (int ax = 0; ax < 3; ++ax)
+        if (!radix_plan(lens[ax], p->rad[ax]) || lens[ax] > kMaxLen) {
+            fail(OPENFFT_ERR_UNSUPPORTED_RADIX, "axis length must factor into 2, 3, 5, 7 and be <= 2048");
+            delete p;
+            return nullptr;
+        }
+    cudaError_t e;
+    if ((e = cudaGetDevice(&p->device))) { cuda_fail(e, "cudaGetDevice"); delete p; return nullptr; }
+    cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
+    if ((e = stage_kernels_init(200 * 1024))) { cuda_fail(e, "kernel attributes"); delete p; return nullptr; }
+    p->elem_bytes = dtype == OPENFFT_C2C_F32 ? 8 : 16;
+    const size_t bytes = (size_t)p->N * p->elem_bytes;
+    if (cudaMalloc(&p->bufA, bytes) || cudaMalloc(&p->bufB, bytes)) {
+        cudaGetLastError();
+        fail(OPENFFT_ERR_NOMEM, "workspace allocation failed");
+        free_plan(p);
+        return nullptr;
+    }
+    // twiddle tables (FP64 sincospi on the device)
+    for (int ax = 0; ax < 3; ++ax) {
+        const int fmts[2] = {dtype == OPENFFT_C2C_F32 ? FMT_C64 : FMT_C128, dtype == OPENFFT_C2C_F32 ? -1 : FMT_DF};
+        for (int f : fmts) {
+            if (f < 0) continue;
+            const size_t eb = f == FMT_C64 ? 8 : 16;
+            if (cudaMalloc(&p->tw[ax][f], eb * (size_t)lens[ax])) {
+                cudaGetLastError();
+                fail(OPENFFT_ERR_NOMEM, "twiddle allocation failed");
+                free_plan(p);
+                return nullptr;
+            }
+            if ((e = launch_twiddles(lens[ax], f, p->tw[ax][f], nullptr))) { cuda_fail(e, "twiddles"); free_plan(p); return nullptr; }
+        }
+    }
+    // transpose tables for the explicit variants
+    const int whichs[4] = {1, 2, -2, -1};
+    for (int i = 0; i < 4; ++i) {
+        TransposeTables& T = p->tt[i];
+        T.t = make_transpose(whichs[i], Na, Nb, Nc, P);
+        std::vector<int64_t> sb, rb, ch;
+        build_transpose_tables(T.t, T.C, sb, rb, ch, 8192);
+        T.nchunks = (int64_t)ch.size() / 3;
+        const size_t pp = sb.size() * sizeof(int64_t);
+        if (cudaMalloc(&T.d_sbase, pp) || cudaMalloc(&T.d_rbase, pp) ||
+            cudaMalloc(&T.d_chunks, ch.size() * sizeof(int64_t) + 8)) {
+            cudaGetLastError();
+            fail(OPENFFT_ERR_NOMEM, "transpose table allocation failed");
+            free_plan(p);
+            return nullptr;
+        }
+        cudaMemcpy(T.d_sbase, sb.data(), pp, cudaMemcpyHostToDevice);
+        cudaMemcpy(T.d_rbase, rb.data(), pp, cudaMemcpyHostToDevice);
+        if (!ch.empty()) cudaMemcpy(T.d_chunks, ch.data(), ch.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    }
+    if ((e = cudaDeviceSynchronize())) { cuda_fail(e, "plan setup"); free_plan(p); return nullptr; }
+    // candidates: (variant, arithmetic, lines per CTA)
+    const int variants[3] = {OPENFFT_VARIANT_FUSED, OPENFFT_VARIANT_PACK_UNPACK, OPENFFT_VARIANT_PACK_EXCHANGE_UNPACK};
+    const int Gs[3] = {8, 16, 4};
+    std::vector<int> ariths;
+    if (dtype == OPENFFT_C2C_F32) ariths = {ARITH_F32};
+    else ariths = {ARITH_F64, ARITH_DF};
+    for (int v : variants)
+        for (int ar : ariths)
+            for (int g : Gs) p->cands.push_back(Candidate{v, ar, g});
+    if (select_candidate(p, 0)) { free_plan(p); return nullptr; }
+    return p;
+}
+
+void openfft_destroy(openfft_plan_t plan)
+{
+    if (!plan) return;
+    cudaStreamSynchronize(plan->stream);
+    free_plan(plan);
+}
+
+int openfft_set_stream(openfft_plan_t plan, void* stream)
+{
+    if (!plan) return fail(OPENFFT_ERR_INVALID_ARG, "null plan");
+    plan->stream = (cudaStream_t)stream;
+    return OPENFFT_OK;
+}
+
+int openfft_exec_c2c(openfft_plan_t plan, const void* in, void* out, int dir)
+{
+    if (!plan || !in || !out) return fail(OPENFFT_ERR_INVALID_ARG, "null plan or buffer");
+    if (in == out) return fail(OPENFFT_ERR_ALIAS, "in and out must differ (out-of-place only)");
+    if (dir != OPENFFT_FORWARD && dir != OPENFFT_BACKWARD) return fail(OPENFFT_ERR_INVALID_ARG, "dir must be -1 or +1");
+    const Candidate& c = plan->cands[(size_t)plan->current];
+    return run_ops(plan, dir == OPENFFT_FORWARD ? plan->ops_fwd : plan->ops_bwd, in, out, c.arith);
+}
+
+int openfft_exec_c2c_host(openfft_plan_t plan, const void* host_in, void* host_out, int dir)
+{
+    if (!plan || !host_in || !host_out) return fail(OPENFFT_ERR_INVALID_ARG, "null plan or buffer");
+    const size_t bytes = (size_t)plan->N * (plan->dtype == OPENFFT_C2C_F32 ? 8 : 16);
+    if (!plan->stage_in) {
+        if (cudaMalloc(&plan->stage_in, bytes) || cudaMalloc(&plan->stage_out, bytes)) {
+            cudaGetLastError();
+            return fail(OPENFFT_ERR_NOMEM, "staging allocation failed");
+        }
+    }
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(plan->stage_in, host_in, bytes, cudaMemcpyHostToDevice, plan->stream))) return cuda_fail(e, "H2D");
+    int st = openfft_exec_c2c(plan, plan->stage_in, plan->stage_out, dir);
+    if (st) return st;
+    if ((e = cudaMemcpyAsync(host_out, plan->stage_out, bytes, cudaMemcpyDeviceToHost, plan->stream))) return cuda_fail(e, "D2H");
+    if ((e = cudaStreamSynchronize(plan->stream))) return cuda_fail(e, "sync");
+    return OPENFFT_OK;
+}
+
+int openfft_sync(openfft_plan_t plan)
+{
+    if (!plan) return fail(OPENFFT_ERR_INVALID_ARG, "null plan");
+    cudaError_t e = cudaStreamSynchronize(plan->stream);
+    if (e) return cuda_fail(e, "stream synchronize");
+    return OPENFFT_OK;
+}
+
+int openfft_box(openfft_plan_t plan, int which, int rank, int64_t start[3], int64_t end[3],
+                int64_t* offset, int64_t* count)
+{
+    if (!plan) return fail(OPENFFT_ERR_INVALID_ARG, "null plan");
+    if (which != 0 && which != 1) return fail(OPENFFT_ERR_INVALID_ARG, "which must be 0 (abc) or 1 (cba)");
+    return box_of(ordering_of(which == 0 ? ABC : CBA, plan->Na, plan->Nb, plan->Nc, plan->P),
+                  rank, start, end, offset, count);
+}
+
+int openfft_counts(openfft_plan_t plan, int exchange, int64_t* PxP)
+{
+    if (!plan || !PxP) return fail(OPENFFT_ERR_INVALID_ARG, "null plan or output");
+    if (exchange != 1 && exchange != 2 && exchange != -1 && exchange != -2)
+        return fail(OPENFFT_ERR_INVALID_ARG, "exchange must be 1, 2, -2 or -1");
+    const std::vector<int64_t>& C = plan->tt[tix_of(exchange)].C;
+    std::memcpy(PxP, C.data(), C.size() * sizeof(int64_t));
+    return OPENFFT_OK;
+}
+
+int openfft_num_candidates(openfft_plan_t plan) { return plan ? (int)plan->cands.size() : 0; }
+
+int openfft_candidate(openfft_plan_t plan, int index, int* variant, int* arith, int* lines_per_cta, int* threads)
+{
+    if (!plan || index < 0 || index >= (int)plan->cands.size()) return fail(OPENFFT_ERR_INVALID_ARG, "bad candidate");
+    const Candidate& c = plan->cands[(size_t)index];
+    if (variant) *variant = c.variant;
+    if (arith) *arith = c.arith == ARITH_DF ? OPENFFT_ARITH_DOUBLE_FLOAT : OPENFFT_ARITH_NATIVE;
+    if (lines_per_cta) *lines_per_cta = c.G;
+    if (threads) *threads = kStageThreads;
+    return OPENFFT_OK;
+}
+
+int openfft_current_candidate(openfft_plan_t plan) { return plan ? plan->current : -1; }
+
+int openfft_set_tuning(openfft_plan_t plan, int mode, int candidate)
+{
+    if (!plan) return fail(OPENFFT_ERR_INVALID_ARG, "null plan");
+    switch (mode) {
+    case OPENFFT_TUNE_DEFAULT:
+    case OPENFFT_TUNE_LEARNED:
+        return select_candidate(plan, 0);
+    case OPENFFT_TUNE_USER:
+        return select_candidate(plan, candidate);
+    case OPENFFT_TUNE_EXHAUSTIVE: {
+        const size_t bytes = (size_t)plan->N * (plan->dtype == OPENFFT_C2C_F32 ? 8 : 16);
+        void *tin = nullptr, *tout = nullptr;
+        if (cudaMalloc(&tin, bytes) || cudaMalloc(&tout, bytes)) {
+            cudaGetLastError(); cudaFree(tin);
+            return fail(OPENFFT_ERR_NOMEM, "tuning buffers");
+        }
+        cudaMemsetAsync(tin, 0, bytes, plan->stream);
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0); cudaEventCreate(&e1);
+        int best = -1; float best_ms = 0.f;
+        int st = OPENFFT_OK;
+        for (int i = 0; i < (int)plan->cands.size() && !st; ++i) {
+            if (select_candidate(plan, i)) { st = OPENFFT_OK; g_status = OPENFFT_OK; continue; }
+            float ms_min = 1e30f;
+            for (int rep = 0; rep < 2 && !st; ++rep) {        // Sec. 3.2.3: each method twice
+                cudaEventRecord(e0, plan->stream);
+                st = openfft_exec_c2c(plan, tin, tout, OPENFFT_FORWARD);
+                cudaEventRecord(e1, plan->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms_min = ms < ms_min ? ms : ms_min;
+            }
+            if (!st && (best < 0 || ms_min < best_ms)) { best = i; best_ms = ms_min; }
+        }
+        cudaEventDestroy(e0); cudaEventDestroy(e1);
+        cudaFree(tin); cudaFree(tout);
+        if (st) return st;
+        if (best < 0) return fail(OPENFFT_ERR_UNSUPPORTED, "no candidate ran");
+        return select_candidate(plan, best);
+    }
+    default:
+        return fail(OPENFFT_ERR_INVALID_ARG, "unknown tuning mode");
+    }
+}
+
+int openfft_set_timing(openfft_plan_t plan, int enable)
+{
+    if (!plan) return fail(OPENFFT_ERR_INVALID_ARG, "null plan");
+    if (enable && plan->ev.empty()) {
+        plan->ev.resize(4096);
+        plan->ev_cat.resize(4096);
+        for (cudaEvent_t& e : plan->ev) {
+            cudaError_t err = cudaEventCreate(&e);
+            if (err) return cuda_fail(err, "cudaEventCreate");
+        }
+    }
+    if (!enable && plan->timing) { int st = fold_timing(plan); if (st) return st; }
+    plan->timing = enable != 0;
+    return OPENFFT_OK;
+}
+
+int openfft_get_timing(openfft_plan_t plan, double ms[4], int64_t launches[4])
+{
+    if (!plan || !ms || !launches) return fail(OPENFFT_ERR_INVALID_ARG, "null plan or output");
+    int st = fold_timing(plan);
+    if (st) return st;
+    for (int i = 0; i < 4; ++i) {
+        ms[i] = plan->t_ms[i]; launches[i] = plan->t_launch[i];
+        plan->t_ms[i] = 0; plan->t_launch[i] = 0;
+    }
+    return OPENFFT_OK;
+}
+
+int openfft_redistribute(openfft_plan_t plan, int exchange, int variant, const void* in, void* out)
+{
+    if (!plan || !in || !out) return fail(OPENFFT_ERR_INVALID_ARG, "null plan or buffer");
+    if (in == out) return fail(OPENFFT_ERR_ALIAS, "in and out must differ");
+    if (exchange != 1 && exchange != 2 && exchange != -1 && exchange != -2)
+        return fail(OPENFFT_ERR_INVALID_ARG, "exchange must be 1, 2, -2 or -1");
+    const int64_t Na = plan->Na, Nb = plan->Nb, Nc = plan->Nc;
+    const int E = (int)plan->elem_bytes;
+    const int ar = plan->dtype == OPENFFT_C2C_F32 ? ARITH_F32 : ARITH_F64;
+    const int fmt = ar == ARITH_F32 ? FMT_C64 : FMT_C128;
+    const TransposeTables& T = plan->tt[tix_of(exchange)];
+    cudaError_t e = cudaSuccess;
+    if (variant == OPENFFT_VARIANT_FUSED) {
+        // the stage kernel with its radix passes switched off: the fused store alone
+        StageLaunch L;
+        int st;
+        switch (exchange) {
+        case 1: st = make_stage(plan, 2, ar, 8, Na * Nb, 1, 1, 0, Na * Nb, 0, 0, fmt, fmt, 0, 0, 1.0, 0, L); break;
+        case 2: st = make_stage(plan, 1, ar, 8, Na, Nc, 1, Nb * Na, Na, 0, 0, fmt, fmt, 0, 0, 1.0, 0, L); break;
+        case -2: st = make_stage(plan, 0, ar, 8, Nb, Nc, 1, Na * Nb, Nb, 0, 0, fmt, fmt, 0, 0, 1.0, 0, L); break;
+        default: st = make_stage(plan, 1, ar, 8, Na, Nc, Nb * Nc, 1, Nc, 1, 0, fmt, fmt, 0, 0, 1.0, 0, L); break;
+        }
+        if (st) return st;
+        L.args.in = in; L.args.out = out;
+        e = launch_stage(L, plan->stream);
+    } else if (variant == OPENFFT_VARIANT_PACK_EXCHANGE_UNPACK) {
+        if (!(e = launch_pack(T.t, E, in, plan->bufA, T.d_sbase, plan->N, plan->sms, plan->stream)))
+            if (!(e = launch_exchange(E, T.d_chunks, T.nchunks, plan->bufA, plan->bufB, plan->sms, plan->stream)))
+                e = launch_unpack(T.t, E, plan->bufB, out, T.d_rbase, 0, plan->N, plan->sms, plan->stream);
+    } else if (variant == OPENFFT_VARIANT_PACK_UNPACK) {
+        if (!(e = launch_pack(T.t, E, in, plan->bufA, T.d_sbase, plan->N, plan->sms, plan->stream)))
+            e = launch_unpack(T.t, E, plan->bufA, out, T.d_sbase, 1, plan->N, plan->sms, plan->stream);
+    } else {
+        return fail(OPENFFT_ERR_INVALID_ARG, "unknown variant");
+    }
+    if (e) return cuda_fail(e, "redistribution launch");
+    return OPENFFT_OK;
+}
+
+}  // extern "C"

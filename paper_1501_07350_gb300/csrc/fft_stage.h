@@ -1,0 +1,49 @@
+// fft_stage.h -- host-visible description of one FFT stage launch.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ofg {
+
+constexpr int kStageThreads = 256;     // threads per CTA of the stage kernel
+constexpr int kMaxLinesPerCta = 32;    // G <= 32
+constexpr int kMaxPasses = 16;
+constexpr int kMaxLen = 2048;          // longest supported axis (two tiles of one line fit in smem)
+
+// element formats in global memory
+enum { FMT_C128 = 0, FMT_C64 = 1, FMT_DF = 2 };
+// arithmetic
+enum { ARITH_F64 = 0, ARITH_F32 = 1, ARITH_DF = 2 };
+
+// Lines of a stage are l = i1 + i2 * M1 (i1 < M1, i2 < M2), each contiguous
+// of length n at in + l * n.  Output element (l, k) goes to
+// out[i1 * S1 + i2 * S2 + k * Sk].  A CTA takes G consecutive values of i1
+// (group_i2 = 0) or of i2 (group_i2 = 1), the coordinate whose output stride
+// is 1, so a store at fixed k writes G consecutive elements.
+struct StageArgs {
+    const void* in;
+    void* out;
+    const void* tw;            // twiddle table of length n (W[e] = exp(-2 pi i e / n))
+    int64_t M1, M2, S1, S2, Sk;
+    int64_t ngroups;           // ceil(M_grouped / G)
+    double scale;              // applied at store (1.0 = none)
+    int n, G, log2G;
+    int group_i2, contig_store;
+    int npass;
+    int radix[kMaxPasses];
+    int conj_in, conj_out, do_fft;
+    int in_fmt, out_fmt;
+};
+
+struct StageLaunch {
+    StageArgs args;
+    int arith;
+    int64_t grid;
+    size_t smem;
+};
+
+cudaError_t stage_kernels_init(int max_dyn_smem);
+cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st);
+cudaError_t launch_twiddles(int n, int fmt, void* out, cudaStream_t st);
+
+}  // namespace ofg

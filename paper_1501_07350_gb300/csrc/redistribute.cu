@@ -1,0 +1,165 @@
+// redistribute.cu -- the explicit transpose variants V0 and V1: steps (4)-(6)
+// of OpenFFT's execution flow (Duy & Ozaki, Sec. 3.1.1) among P logical ranks
+// that share one GPU's memory.
+//
+//   pack      (step 4): every element of the source ordering is written into
+//             the send segment (r -> s) of its owner r, at its rank in
+//             ascending source index inside that segment;
+//   exchange  (step 5): every segment is copied to the receive buffer of s,
+//             segments from lower source ranks first (one all-to-all with
+//             variable counts, the Alltoallv / Isend-Irecv-Waitall methods);
+//   unpack    (step 6): every element of the destination ordering is read from
+//             the receive buffer (V0) or straight from the sender's segment
+//             (V1, the unpack-on-arrival of Isend_Waitsome) and stored in place.
+//
+// Positions come from the closed forms of decomp.h; per rank pair the plan
+// precomputes base offsets so each element needs only its own row's prefix.
+#include "redistribute.h"
+
+namespace ofg {
+
+template <class E>
+__global__ void pack_kernel(const Transpose t, const E* __restrict__ src, E* __restrict__ send,
+                            const int64_t* __restrict__ sbase, int64_t N)
+{
+    const int64_t P = t.src.P;
+    const int64_t Ls = row_len(t), Ld = dst_row_len(t);
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < N;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = x / Ls, e = x - q * Ls;
+        const int64_t r = row_owner(t.src, q);
+        const int64_t y = dest_index(t, q, e);
+        const int64_t s = row_owner(t.dst, y / Ld);
+        const int64_t Q0 = row_begin(t.dst, s), Q1 = row_begin(t.dst, s + 1);
+        int64_t e_lo, cnt;
+        row_range(t, q, Q0, Q1, &e_lo, &cnt);
+        const int64_t pos = sbase[r * P + s] + prefix_to(t, q, Q0, Q1) + (e - e_lo);
+        send[pos] = src[x];
+    }
+}
+
+// chunks: (src offset, dst offset, length) triples, one CTA per chunk
+template <class E>
+__global__ void exchange_kernel(const int64_t* __restrict__ chunks, int64_t nchunks,
+                                const E* __restrict__ send, E* __restrict__ recv)
+{
+    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const int64_t so = chunks[3 * c], ro = chunks[3 * c + 1], len = chunks[3 * c + 2];
+        for (int64_t j = threadIdx.x; j < len; j += blockDim.x) recv[ro + j] = send[so + j];
+    }
+}
+
+// from_send = 0: buf is the receive buffer, base indexed [s * P + r];
+// from_send = 1: buf is the send buffer,    base indexed [r * P + s].
+template <class E>
+__global__ void unpack_kernel(const Transpose t, const E* __restrict__ buf, E* __restrict__ dst,
+                              const int64_t* __restrict__ base, int from_send, int64_t N)
+{
+    const int64_t P = t.src.P;
+    const int64_t Ld = dst_row_len(t);
+    for (int64_t y = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; y < N;
+         y += (int64_t)gridDim.x * blockDim.x) {
+        int64_t q, e;
+        source_of(t, y, &q, &e);
+        const int64_t r = row_owner(t.src, q);
+        const int64_t s = row_owner(t.dst, y / Ld);
+        const int64_t Q0 = row_begin(t.dst, s), Q1 = row_begin(t.dst, s + 1);
+        int64_t e_lo, cnt;
+        row_range(t, q, Q0, Q1, &e_lo, &cnt);
+        const int64_t rank = prefix_to(t, q, Q0, Q1) + (e - e_lo);
+        const int64_t b = from_send ? base[r * P + s] : base[s * P + r];
+        dst[y] = buf[b + rank];
+    }
+}
+
+static unsigned grid_for(int64_t N, int sms)
+{
+    int64_t want = (N + 255) / 256;
+    int64_t cap = (int64_t)sms * 16;
+    return (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+cudaError_t launch_pack(const Transpose& t, int elem_bytes, const void* src, void* send,
+                        const int64_t* sbase, int64_t N, int sms, cudaStream_t st)
+{
+    if (N == 0) return cudaSuccess;
+    if (elem_bytes == 16)
+        pack_kernel<uint4><<<grid_for(N, sms), 256, 0, st>>>(t, (const uint4*)src, (uint4*)send, sbase, N);
+    else
+        pack_kernel<uint2><<<grid_for(N, sms), 256, 0, st>>>(t, (const uint2*)src, (uint2*)send, sbase, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exchange(int elem_bytes, const int64_t* chunks, int64_t nchunks,
+                            const void* send, void* recv, int sms, cudaStream_t st)
+{
+    if (nchunks == 0) return cudaSuccess;
+    int64_t cap = (int64_t)sms * 16;
+    unsigned grid = (unsigned)(nchunks < cap ? nchunks : cap);
+    if (elem_bytes == 16)
+        exchange_kernel<uint4><<<grid, 256, 0, st>>>(chunks, nchunks, (const uint4*)send, (uint4*)recv);
+    else
+        exchange_kernel<uint2><<<grid, 256, 0, st>>>(chunks, nchunks, (const uint2*)send, (uint2*)recv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const Transpose& t, int elem_bytes, const void* buf, void* dst,
+                          const int64_t* base, int from_send, int64_t N, int sms, cudaStream_t st)
+{
+    if (N == 0) return cudaSuccess;
+    if (elem_bytes == 16)
+        unpack_kernel<uint4><<<grid_for(N, sms), 256, 0, st>>>(t, (const uint4*)buf, (uint4*)dst, base, from_send, N);
+    else
+        unpack_kernel<uint2><<<grid_for(N, sms), 256, 0, st>>>(t, (const uint2*)buf, (uint2*)dst, base, from_send, N);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ host tables --
+
+void build_transpose_tables(const Transpose& t, std::vector<int64_t>& C, std::vector<int64_t>& sbase,
+                            std::vector<int64_t>& rbase, std::vector<int64_t>& chunks, int64_t chunk_len)
+{
+    const int64_t P = t.src.P;
+    C.assign((size_t)(P * P), 0);
+    std::vector<int64_t> pre((size_t)(P * P));   // prefix_to(R0_r) for destination s
+    for (int64_t r = 0; r < P; ++r)
+        for (int64_t s = 0; s < P; ++s) {
+            const int64_t Q0 = row_begin(t.dst, s), Q1 = row_begin(t.dst, s + 1);
+            const int64_t R0 = row_begin(t.src, r), R1 = row_begin(t.src, r + 1);
+            const int64_t a = prefix_to(t, R0, Q0, Q1);
+            C[(size_t)(r * P + s)] = prefix_to(t, R1, Q0, Q1) - a;
+            pre[(size_t)(r * P + s)] = a;
+        }
+    sbase.assign((size_t)(P * P), 0);
+    rbase.assign((size_t)(P * P), 0);
+    std::vector<int64_t> sdispl((size_t)(P * P)), rdispl((size_t)(P * P));
+    for (int64_t r = 0; r < P; ++r) {
+        int64_t off = box_begin(t.src, r);
+        for (int64_t s = 0; s < P; ++s) {
+            sdispl[(size_t)(r * P + s)] = off;
+            sbase[(size_t)(r * P + s)] = off - pre[(size_t)(r * P + s)];
+            off += C[(size_t)(r * P + s)];
+        }
+    }
+    for (int64_t s = 0; s < P; ++s) {
+        int64_t off = box_begin(t.dst, s);
+        for (int64_t r = 0; r < P; ++r) {
+            rdispl[(size_t)(s * P + r)] = off;
+            rbase[(size_t)(s * P + r)] = off - pre[(size_t)(r * P + s)];
+            off += C[(size_t)(r * P + s)];
+        }
+    }
+    chunks.clear();
+    for (int64_t s = 0; s < P; ++s)
+        for (int64_t r = 0; r < P; ++r) {
+            int64_t len = C[(size_t)(r * P + s)];
+            int64_t so = sdispl[(size_t)(r * P + s)], ro = rdispl[(size_t)(s * P + r)];
+            for (int64_t j = 0; j < len; j += chunk_len) {
+                chunks.push_back(so + j);
+                chunks.push_back(ro + j);
+                chunks.push_back(len - j < chunk_len ? len - j : chunk_len);
+            }
+        }
+}
+
+}  // namespace ofg

@@ -1,0 +1,246 @@
+"""Thin ctypes binding of the C ABI in include/openfft_gb.h.
+
+Argument marshalling only: every step of the transform runs in the CUDA
+kernels of libopenfft_gb.so.  Device buffers are passed as torch CUDA tensors
+(or raw integer device pointers); torch provides memory and streams only.
+There is no fallback: if the shared library has not been built, loading
+raises an error that says how to build it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+OK = 0
+ERR_INVALID_ARG, ERR_P_TOO_LARGE, ERR_UNSUPPORTED_RADIX, ERR_CUDA, ERR_NOMEM = 1, 2, 3, 4, 5
+ERR_TIMEOUT, ERR_ALIAS, ERR_UNSUPPORTED = 6, 7, 8
+
+C2C_F64, C2C_F32, C2C_SPLIT_BF16, C2C_SPLIT_TF32 = 0, 1, 2, 3
+FORWARD, BACKWARD = -1, 1
+VARIANT_PACK_EXCHANGE_UNPACK, VARIANT_PACK_UNPACK, VARIANT_FUSED = 0, 1, 2
+ARITH_NATIVE, ARITH_DOUBLE_FLOAT = 0, 1
+TUNE_DEFAULT, TUNE_EXHAUSTIVE, TUNE_LEARNED, TUNE_USER = 0, 1, 2, 3
+LAYOUT_ABC, LAYOUT_CAB, LAYOUT_CBA = 0, 1, 2
+
+# every symbol declared in include/openfft_gb.h
+EXPORTS = [
+    "openfft_plan", "openfft_exec_c2c", "openfft_exec_c2c_host", "openfft_destroy", "openfft_sync",
+    "openfft_set_stream", "openfft_last_error", "openfft_last_status", "openfft_box", "openfft_counts",
+    "openfft_decomp_box", "openfft_decomp_counts", "openfft_decomp_degree", "openfft_set_tuning",
+    "openfft_num_candidates", "openfft_candidate", "openfft_current_candidate", "openfft_redistribute",
+    "openfft_set_timing", "openfft_get_timing",
+]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class OpenFFTError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("openfft status %d: %s" % (status, message))
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load():
+    """Load libopenfft_gb.so (build it first with __graft_entry__.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB_PATH
+        if not os.path.exists(path):
+            raise RuntimeError("libopenfft_gb.so is not built (%s); run `python -c \"import "
+                               "__graft_entry__ as g; g.build()\"`" % path)
+        lib = ctypes.CDLL(path)
+        i32, i64, vp = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+        p64 = ctypes.POINTER(ctypes.c_int64)
+        pi32 = ctypes.POINTER(ctypes.c_int)
+        sig = {
+            "openfft_plan": (vp, [i32, i32, i32, i32, i32]),
+            "openfft_exec_c2c": (i32, [vp, vp, vp, i32]),
+            "openfft_exec_c2c_host": (i32, [vp, vp, vp, i32]),
+            "openfft_destroy": (None, [vp]),
+            "openfft_sync": (i32, [vp]),
+            "openfft_set_stream": (i32, [vp, vp]),
+            "openfft_last_error": (ctypes.c_char_p, []),
+            "openfft_last_status": (i32, []),
+            "openfft_box": (i32, [vp, i32, i32, p64, p64, p64, p64]),
+            "openfft_counts": (i32, [vp, i32, p64]),
+            "openfft_decomp_box": (i32, [i32, i32, i32, i32, i32, i32, p64, p64, p64, p64]),
+            "openfft_decomp_counts": (i32, [i32, i32, i32, i32, i32, p64]),
+            "openfft_decomp_degree": (i32, [i32, i32, i32, i32, i32]),
+            "openfft_set_tuning": (i32, [vp, i32, i32]),
+            "openfft_num_candidates": (i32, [vp]),
+            "openfft_candidate": (i32, [vp, i32, pi32, pi32, pi32, pi32]),
+            "openfft_current_candidate": (i32, [vp]),
+            "openfft_redistribute": (i32, [vp, i32, i32, vp, vp]),
+            "openfft_set_timing": (i32, [vp, i32]),
+            "openfft_get_timing": (i32, [vp, ctypes.POINTER(ctypes.c_double), p64]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def last_error() -> str:
+    return load().openfft_last_error().decode()
+
+
+def _check(status: int):
+    if status != OK:
+        raise OpenFFTError(status, last_error())
+
+
+def _ptr(x) -> int:
+    """Device pointer of a torch tensor (or an int passed through)."""
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+# ------------------------------------------------ same names as the C ABI --
+
+def openfft_plan(Na: int, Nb: int, Nc: int, P: int, dtype: int) -> int:
+    h = load().openfft_plan(Na, Nb, Nc, P, dtype)
+    if not h:
+        raise OpenFFTError(load().openfft_last_status(), last_error())
+    return h
+
+
+def openfft_exec_c2c(plan: int, inp, out, direction: int) -> None:
+    _check(load().openfft_exec_c2c(plan, _ptr(inp), _ptr(out), direction))
+
+
+def openfft_exec_c2c_host(plan: int, host_in: np.ndarray, host_out: np.ndarray, direction: int) -> None:
+    _check(load().openfft_exec_c2c_host(plan, host_in.ctypes.data, host_out.ctypes.data, direction))
+
+
+def openfft_destroy(plan: int) -> None:
+    load().openfft_destroy(plan)
+
+
+def openfft_sync(plan: int) -> None:
+    _check(load().openfft_sync(plan))
+
+
+def openfft_set_stream(plan: int, stream) -> None:
+    """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+    raw = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(load().openfft_set_stream(plan, raw))
+
+
+def openfft_box(plan: int, which: int, rank: int):
+    s = (ctypes.c_int64 * 3)()
+    e = (ctypes.c_int64 * 3)()
+    off, cnt = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().openfft_box(plan, which, rank, s, e, ctypes.byref(off), ctypes.byref(cnt)))
+    return tuple(s), tuple(e), off.value, cnt.value
+
+
+def openfft_counts(plan: int, exchange: int, P: int) -> np.ndarray:
+    C = np.zeros((P, P), dtype=np.int64)
+    _check(load().openfft_counts(plan, exchange, C.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return C
+
+
+def openfft_decomp_box(Na, Nb, Nc, P, layout, rank):
+    s = (ctypes.c_int64 * 3)()
+    e = (ctypes.c_int64 * 3)()
+    off, cnt = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().openfft_decomp_box(Na, Nb, Nc, P, layout, rank, s, e, ctypes.byref(off), ctypes.byref(cnt)))
+    return tuple(s), tuple(e), off.value, cnt.value
+
+
+def openfft_decomp_counts(Na, Nb, Nc, P, exchange) -> np.ndarray:
+    C = np.zeros((P, P), dtype=np.int64)
+    _check(load().openfft_decomp_counts(Na, Nb, Nc, P, exchange, C.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return C
+
+
+def openfft_decomp_degree(Na, Nb, Nc, P, layout) -> int:
+    return int(load().openfft_decomp_degree(Na, Nb, Nc, P, layout))
+
+
+def openfft_set_tuning(plan: int, mode: int, candidate: int = 0) -> None:
+    _check(load().openfft_set_tuning(plan, mode, candidate))
+
+
+def openfft_num_candidates(plan: int) -> int:
+    return int(load().openfft_num_candidates(plan))
+
+
+def openfft_candidate(plan: int, index: int):
+    v, a, g, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().openfft_candidate(plan, index, ctypes.byref(v), ctypes.byref(a), ctypes.byref(g), ctypes.byref(t)))
+    return {"variant": v.value, "arith": a.value, "lines_per_cta": g.value, "threads": t.value}
+
+
+def openfft_current_candidate(plan: int) -> int:
+    return int(load().openfft_current_candidate(plan))
+
+
+def openfft_redistribute(plan: int, exchange: int, variant: int, inp, out) -> None:
+    _check(load().openfft_redistribute(plan, exchange, variant, _ptr(inp), _ptr(out)))
+
+
+def openfft_set_timing(plan: int, enable: bool) -> None:
+    _check(load().openfft_set_timing(plan, 1 if enable else 0))
+
+
+PHASES = ("fft", "buffer_comm", "communication", "exec")
+
+
+def openfft_get_timing(plan: int) -> dict:
+    """Per-phase milliseconds and launch counts since the previous call."""
+    ms = (ctypes.c_double * 4)()
+    n = (ctypes.c_int64 * 4)()
+    _check(load().openfft_get_timing(plan, ms, n))
+    return {name: {"ms": ms[i], "launches": n[i]} for i, name in enumerate(PHASES)}
+
+
+# ------------------------------------------------------- convenience ----
+
+class Plan:
+    """RAII wrapper: ``with Plan(Na, Nb, Nc, P, dtype) as p: p.exec(x, y, FORWARD)``.
+
+    Uses torch's current CUDA stream unless ``stream`` is given."""
+
+    def __init__(self, Na, Nb, Nc, P, dtype=C2C_F64, stream=None):
+        import torch
+        self.shape = (Na, Nb, Nc)
+        self.P = P
+        self.dtype = dtype
+        self.handle = openfft_plan(Na, Nb, Nc, P, dtype)
+        openfft_set_stream(self.handle, stream if stream is not None else torch.cuda.current_stream())
+
+    def exec(self, inp, out, direction=FORWARD):
+        openfft_exec_c2c(self.handle, inp, out, direction)
+
+    def close(self):
+        if self.handle:
+            openfft_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

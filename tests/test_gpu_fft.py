@@ -1,0 +1,256 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Bars (fixed before the first GPU run):
+  - transposes: bit-exact (they move bytes);
+  - FP64 plans (native and double-float arithmetic): relative L2 <= 1e-12;
+  - FP32 plans: relative L2 <= 1e-5 against the FP64 oracle on the same input.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1501_07350_gb300 import openfft as of
+from paper_1501_07350_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_F64 = 1e-12
+TOL_F32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    from paper_1501_07350_gb300 import _build
+    _build.build()
+    of.load()
+    assert _t.cuda.is_available()
+    return _t
+
+
+def _run(torch, plan, x, direction, dtype):
+    tdt = torch.complex128 if dtype == of.C2C_F64 else torch.complex64
+    xd = torch.from_numpy(np.ascontiguousarray(x.reshape(-1))).to(device="cuda", dtype=tdt)
+    yd = torch.empty_like(xd)
+    of.openfft_set_stream(plan, torch.cuda.current_stream())
+    of.openfft_exec_c2c(plan, xd, yd, direction)
+    of.openfft_sync(plan)
+    out = yd.cpu().numpy()
+    # the input must be left unchanged (out of place)
+    assert np.array_equal(xd.cpu().numpy(), x.reshape(-1).astype(out.dtype))
+    return out.astype(np.complex128)
+
+
+def _all_candidates(plan):
+    return range(of.openfft_num_candidates(plan))
+
+
+# ---------------------------------------------------- 32^3, P = 4 ------
+
+def test_32cubed_p4_every_candidate(torch):
+    Na = Nb = Nc = 32
+    x = synth.complex_field((Na, Nb, Nc), seed=synth.config_seed(1))
+    ref = oracle.fft3d(x, Na, Nb, Nc, 4, oracle.FORWARD)
+    back_ref = x.reshape(-1)
+    plan = of.openfft_plan(Na, Nb, Nc, 4, of.C2C_F64)
+    try:
+        for c in _all_candidates(plan):
+            of.openfft_set_tuning(plan, of.TUNE_USER, c)
+            y = _run(torch, plan, x, of.FORWARD, of.C2C_F64)
+            assert oracle.rel_l2(y, ref) < TOL_F64, (c, of.openfft_candidate(plan, c))
+            z = _run(torch, plan, y, of.BACKWARD, of.C2C_F64)
+            assert oracle.rel_l2(z, back_ref) < TOL_F64, (c, of.openfft_candidate(plan, c))
+    finally:
+        of.openfft_destroy(plan)
+
+
+# ------------------------------------------ small and ragged shapes -----
+
+SMALL = [((1, 1, 1), 1), ((1, 8, 1), 1), ((2, 3, 5), 2), ((4, 6, 5), 3), ((8, 3, 5), 5), ((5, 4, 3), 12),
+         ((12, 10, 9), 30), ((9, 25, 14), 7), ((36, 40, 30), 64), ((7, 49, 6), 42), ((3, 1, 2), 2),
+         ((16, 16, 16), 256), ((64, 48, 100), 33)]
+
+
+@pytest.mark.parametrize("shape,P", SMALL)
+def test_small_shapes_f64_every_candidate(torch, shape, P):
+    Na, Nb, Nc = shape
+    x = synth.complex_field(shape, seed=Na * 1000 + Nb * 10 + Nc)
+    ref = oracle.fft3d(x, Na, Nb, Nc, P, oracle.FORWARD)
+    refb = oracle.fft3d(x, Na, Nb, Nc, P, oracle.BACKWARD)      # x read as a cba spectrum
+    plan = of.openfft_plan(Na, Nb, Nc, P, of.C2C_F64)
+    try:
+        for c in _all_candidates(plan):
+            of.openfft_set_tuning(plan, of.TUNE_USER, c)
+            y = _run(torch, plan, x, of.FORWARD, of.C2C_F64)
+            assert oracle.rel_l2(y, ref) < TOL_F64, (shape, P, of.openfft_candidate(plan, c))
+            z = _run(torch, plan, x, of.BACKWARD, of.C2C_F64)
+            assert oracle.rel_l2(z, refb) < TOL_F64, (shape, P, of.openfft_candidate(plan, c))
+    finally:
+        of.openfft_destroy(plan)
+
+
+@pytest.mark.parametrize("shape,P", [((32, 32, 32), 4), ((12, 10, 9), 30), ((36, 40, 30), 64), ((5, 4, 3), 12)])
+def test_small_shapes_f32_every_candidate(torch, shape, P):
+    Na, Nb, Nc = shape
+    x = synth.complex_field(shape, seed=77).astype(np.complex64)
+    ref = oracle.fft3d(x.astype(np.complex128), Na, Nb, Nc, P, oracle.FORWARD)
+    plan = of.openfft_plan(Na, Nb, Nc, P, of.C2C_F32)
+    try:
+        for c in _all_candidates(plan):
+            of.openfft_set_tuning(plan, of.TUNE_USER, c)
+            y = _run(torch, plan, x, of.FORWARD, of.C2C_F32)
+            assert oracle.rel_l2(y, ref) < TOL_F32, (shape, P, of.openfft_candidate(plan, c))
+            z = _run(torch, plan, y.astype(np.complex64), of.BACKWARD, of.C2C_F32)
+            assert oracle.rel_l2(z, x.reshape(-1).astype(np.complex128)) < TOL_F32
+    finally:
+        of.openfft_destroy(plan)
+
+
+# ----------------------------------------------- 120 x 144 x 160, P = 32 --
+
+def test_mixed_radix_120x144x160(torch):
+    Na, Nb, Nc = 120, 144, 160
+    x = synth.complex_field((Na, Nb, Nc), seed=synth.config_seed(3))
+    ref = oracle.fft3d(x, Na, Nb, Nc, 32, oracle.FORWARD)
+    plan = of.openfft_plan(Na, Nb, Nc, 32, of.C2C_F64)
+    try:
+        for c in _all_candidates(plan):
+            cand = of.openfft_candidate(plan, c)
+            if cand["variant"] != of.VARIANT_FUSED and cand["lines_per_cta"] != 8:
+                continue
+            of.openfft_set_tuning(plan, of.TUNE_USER, c)
+            y = _run(torch, plan, x, of.FORWARD, of.C2C_F64)
+            assert oracle.rel_l2(y, ref) < TOL_F64, cand
+    finally:
+        of.openfft_destroy(plan)
+    plan = of.openfft_plan(Na, Nb, Nc, 32, of.C2C_F32)
+    try:
+        y = _run(torch, plan, x.astype(np.complex64), of.FORWARD, of.C2C_F32)
+        assert oracle.rel_l2(y, ref) < TOL_F32
+    finally:
+        of.openfft_destroy(plan)
+
+
+@pytest.mark.parametrize("k0", [(0, 0, 0), (1, 2, 3), (59, 71, 79), (119, 143, 159)])
+def test_plane_waves_120x144x160(torch, k0):
+    Na, Nb, Nc = 120, 144, 160
+    N = Na * Nb * Nc
+    x = synth.plane_wave(Na, Nb, Nc, k0)
+    exact = np.zeros((Na, Nb, Nc), complex)
+    exact[k0] = N
+    exact = oracle.abc_to_cba(exact)
+    for dtype, tol in [(of.C2C_F64, 1e-14), (of.C2C_F32, 1e-6)]:
+        plan = of.openfft_plan(Na, Nb, Nc, 32, dtype)
+        try:
+            xx = x if dtype == of.C2C_F64 else x.astype(np.complex64)
+            y = _run(torch, plan, xx, of.FORWARD, dtype)
+            assert np.linalg.norm(y - exact) / (N * np.sqrt(N)) < tol
+        finally:
+            of.openfft_destroy(plan)
+
+
+# --------------------------------------------------- transposes alone ----
+
+REDIST = [((4, 3, 2), 3), ((4, 3, 2), 6), ((8, 6, 10), 40), ((12, 10, 9), 30), ((5, 7, 3), 15),
+          ((16, 16, 16), 64), ((32, 32, 32), 4), ((20, 18, 15), 7), ((8, 8, 8), 16), ((7, 1, 5), 5)]
+
+
+@pytest.mark.parametrize("shape,P", REDIST)
+def test_transposes_bit_exact(torch, shape, P):
+    Na, Nb, Nc = shape
+    N = Na * Nb * Nc
+    src = synth.complex_field((N,), seed=N + P)
+    plan = of.openfft_plan(Na, Nb, Nc, P, of.C2C_F64)
+    try:
+        of.openfft_set_stream(plan, torch.cuda.current_stream())
+        for which, code in [("abc->cab", 1), ("cab->cba", 2), ("cba->cab", -2), ("cab->abc", -1)]:
+            ref, C = oracle.redistribute(Na, Nb, Nc, P, which, src)
+            assert np.array_equal(of.openfft_counts(plan, code, P), C)
+            for variant in (of.VARIANT_FUSED, of.VARIANT_PACK_UNPACK, of.VARIANT_PACK_EXCHANGE_UNPACK):
+                xd = torch.from_numpy(src).cuda()
+                yd = torch.full_like(xd, float("nan"))
+                of.openfft_redistribute(plan, code, variant, xd, yd)
+                of.openfft_sync(plan)
+                got = yd.cpu().numpy()
+                assert np.array_equal(got.view(np.uint64), ref.view(np.uint64)), (which, variant)
+    finally:
+        of.openfft_destroy(plan)
+
+
+# --------------------------------------------- full sizes, sampled ------
+
+def _sample_lines(x, y_cba, Na, Nb, Nc, picks):
+    for kb, kc in picks:
+        ref = oracle.dft3d_line(x, kb, kc, oracle.FORWARD)
+        got = y_cba[(kc * Nb + kb) * Na:(kc * Nb + kb + 1) * Na]
+        assert oracle.rel_l2(got, ref) < TOL_F64, (kb, kc)
+
+
+@pytest.mark.parametrize("P", [16, 64, 256])
+def test_256cubed_default_plan_sampled(torch, P):
+    n = 256
+    x = synth.complex_field((n, n, n), seed=synth.config_seed(2), dist="normal")
+    plan = of.openfft_plan(n, n, n, P, of.C2C_F64)
+    try:
+        y = _run(torch, plan, x, of.FORWARD, of.C2C_F64)
+        _sample_lines(x, y, n, n, n, [(0, 0), (1, 2), (255, 128), (77, 200)])
+        N = n ** 3
+        assert abs(np.sum(np.abs(y) ** 2) / (N * np.sum(np.abs(x) ** 2)) - 1.0) < 1e-13   # Parseval
+        z = _run(torch, plan, y, of.BACKWARD, of.C2C_F64)
+        assert oracle.rel_l2(z, x.reshape(-1)) < TOL_F64
+    finally:
+        of.openfft_destroy(plan)
+
+
+def test_512cubed_sampled(torch):
+    n = 512
+    x = synth.complex_field((n, n, n), seed=synth.config_seed(5))
+    plan = of.openfft_plan(n, n, n, 1024, of.C2C_F64)
+    try:
+        y = _run(torch, plan, x, of.FORWARD, of.C2C_F64)
+        _sample_lines(x, y, n, n, n, [(3, 5), (511, 256)])
+        z = _run(torch, plan, y, of.BACKWARD, of.C2C_F64)
+        assert oracle.rel_l2(z, x.reshape(-1)) < TOL_F64
+    finally:
+        of.openfft_destroy(plan)
+
+
+# ------------------------------------------------------------ errors ----
+
+def test_argument_errors(torch):
+    with pytest.raises(of.OpenFFTError) as ei:
+        of.openfft_plan(11, 8, 8, 2, of.C2C_F64)
+    assert ei.value.status == of.ERR_UNSUPPORTED_RADIX
+    with pytest.raises(of.OpenFFTError) as ei:
+        of.openfft_plan(8, 8, 8, 65, of.C2C_F64)
+    assert ei.value.status == of.ERR_P_TOO_LARGE
+    plan = of.openfft_plan(8, 8, 8, 2, of.C2C_F64)
+    try:
+        x = torch.zeros(512, dtype=torch.complex128, device="cuda")
+        with pytest.raises(of.OpenFFTError) as ei:
+            of.openfft_exec_c2c(plan, x, x, of.FORWARD)
+        assert ei.value.status == of.ERR_ALIAS
+        with pytest.raises(of.OpenFFTError) as ei:
+            of.openfft_exec_c2c(plan, x, torch.zeros_like(x), 0)
+        assert ei.value.status == of.ERR_INVALID_ARG
+    finally:
+        of.openfft_destroy(plan)
+
+
+def test_host_exec_and_tuning(torch):
+    Na, Nb, Nc = 48, 64, 40
+    x = synth.complex_field((Na, Nb, Nc), seed=4)
+    ref = oracle.fft3d(x, Na, Nb, Nc, 8, oracle.FORWARD)
+    plan = of.openfft_plan(Na, Nb, Nc, 8, of.C2C_F64)
+    try:
+        of.openfft_set_tuning(plan, of.TUNE_EXHAUSTIVE)
+        y = np.empty(Na * Nb * Nc, np.complex128)
+        of.openfft_exec_c2c_host(plan, np.ascontiguousarray(x.reshape(-1)), y, of.FORWARD)
+        assert oracle.rel_l2(y, ref) < TOL_F64
+        of.openfft_set_timing(plan, True)
+        of.openfft_exec_c2c_host(plan, np.ascontiguousarray(x.reshape(-1)), y, of.FORWARD)
+        t = of.openfft_get_timing(plan)
+        assert t["exec"]["launches"] == 1 and t["fft"]["launches"] == 3
+        assert t["fft"]["ms"] > 0
+    finally:
+        of.openfft_destroy(plan)
