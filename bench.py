@@ -408,6 +408,55 @@ def run_reference(args, rank, world):
     print(json.dumps(res), flush=True)
 
 
+def run_single(args, local_rank):
+    """One form on one shape, forward only: a small, fixed command for profilers."""
+    import torch
+
+    from paper_1501_07350_gb300 import _build
+    from paper_1501_07350_gb300 import openfft as of
+    from paper_1501_07350_gb300 import synth
+
+    _build.build()
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    n = args.n
+    N = n ** 3
+    dtype = of.C2C_F32 if args.form == "f32" else of.C2C_F64
+    want_arith = of.ARITH_DOUBLE_FLOAT if args.form == "f64-df" else of.ARITH_NATIVE
+    want_variant = {"fused": of.VARIANT_FUSED, "v1": of.VARIANT_PACK_UNPACK,
+                    "v0": of.VARIANT_PACK_EXCHANGE_UNPACK}[args.variant]
+    x = torch.from_numpy(synth.complex_field((N,), seed=synth.config_seed(2))).cuda()
+    if dtype == of.C2C_F32:
+        x = x.to(torch.complex64)
+    y = torch.empty_like(x)
+    h = of.openfft_plan(n, n, n, args.P, dtype)
+    of.openfft_set_stream(h, stream)
+    pick = None
+    for ci in range(of.openfft_num_candidates(h)):
+        c = of.openfft_candidate(h, ci)
+        if c["variant"] == want_variant and c["arith"] == want_arith and c["lines_per_cta"] == args.G:
+            pick = ci
+    if pick is None:
+        raise SystemExit("no such candidate")
+    of.openfft_set_tuning(h, of.TUNE_USER, pick)
+    for _ in range(args.warmup):
+        of.openfft_exec_c2c(h, x, y, of.FORWARD)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        of.openfft_exec_c2c(h, x, y, of.FORWARD)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    E = 8 if dtype == of.C2C_F32 else 16
+    print(json.dumps({"single": args.form, "n": n, "P": args.P, "variant": args.variant, "G": args.G,
+                      "ms": round(ms, 4), "gflops": round(flops(N) / ms / 1e6, 1),
+                      "hbm_frac": round(6 * N * E / (ms * 1e-3) / 1e9 / load_peaks()[0], 4)}))
+    of.openfft_destroy(h)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -418,6 +467,13 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the other forms")
     ap.add_argument("--no-512", dest="no_512", action="store_true", help="skip the 512^3 form")
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
+    ap.add_argument("--single", action="store_true",
+                    help="time one form on one n^3 shape (forward only), for profiling")
+    ap.add_argument("--form", choices=["f64-native", "f64-df", "f32"], default="f64-df")
+    ap.add_argument("--variant", choices=["fused", "v1", "v0"], default="fused")
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--P", type=int, default=64)
+    ap.add_argument("--G", type=int, default=8)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)     # at least 3 warm-up steps; the count run is reported
     rank = int(os.environ.get("RANK", "0"))
@@ -425,6 +481,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.single:
+        run_single(args, local_rank)
         return
     if world > 1:
         import torch

@@ -147,6 +147,7 @@ int make_stage(openfft_plan_s* p, int axis, int arith, int Gt, int64_t M1, int64
     a.conj_in = conj_in; a.conj_out = conj_out; a.do_fft = do_fft;
     a.in_fmt = in_fmt; a.out_fmt = out_fmt;
     L.arith = arith;
+    L.sms = p->sms;
     L.grid = a.ngroups * (group_i2 ? M1 : M2);
     L.smem = 2 * (size_t)n * (G + 1) * E;     // two ping-pong tiles
     if (L.grid > 0x7fffffffLL) return fail(OPENFFT_ERR_UNSUPPORTED, "grid too large");

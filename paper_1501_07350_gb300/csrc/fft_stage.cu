@@ -22,55 +22,13 @@
 // next radix r (s' = s / r) combines r of them:
 //   Y'[t'][k + m q] = sum_j W_r^{j q} (W_{m r}^{j k} Y[t' + s' j][k]),
 // with W_{m r}^{j k} = W_n^{j k s'} read from the twiddle table of length n.
+#include <type_traits>
+
 #include "fft_stage.h"
 #include "arith.cuh"
+#include "stage_io.cuh"
 
 namespace ofg {
-
-// ------------------------------------------------ element load / store ----
-
-template <class A> struct Io;
-
-template <> struct Io<ArF64> {
-    __device__ __forceinline__ static double2 load(const void* p, int, int64_t i) {
-        return __ldg(reinterpret_cast<const double2*>(p) + i);
-    }
-    __device__ __forceinline__ static void store(void* p, int, int64_t i, double2 v) {
-        reinterpret_cast<double2*>(p)[i] = v;
-    }
-};
-
-template <> struct Io<ArF32> {
-    __device__ __forceinline__ static float2 load(const void* p, int, int64_t i) {
-        return __ldg(reinterpret_cast<const float2*>(p) + i);
-    }
-    __device__ __forceinline__ static void store(void* p, int, int64_t i, float2 v) {
-        reinterpret_cast<float2*>(p)[i] = v;
-    }
-};
-
-// Double-float: external arrays hold complex128; intermediate arrays hold the
-// (hi, lo) pairs themselves (FMT_DF), so conversions happen once on entry and
-// once on exit of the 3-D transform.
-__device__ __forceinline__ float4 df_from_double2(double2 v) {
-    float hr = __double2float_rn(v.x), hi = __double2float_rn(v.y);
-    float lr = __double2float_rn(v.x - (double)hr), li = __double2float_rn(v.y - (double)hi);
-    return make_float4(hr, hi, lr, li);
-}
-__device__ __forceinline__ double2 df_to_double2(float4 v) {
-    return make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
-}
-
-template <> struct Io<ArDF> {
-    __device__ __forceinline__ static float4 load(const void* p, int fmt, int64_t i) {
-        if (fmt == FMT_DF) return __ldg(reinterpret_cast<const float4*>(p) + i);
-        return df_from_double2(__ldg(reinterpret_cast<const double2*>(p) + i));
-    }
-    __device__ __forceinline__ static void store(void* p, int fmt, int64_t i, float4 v) {
-        if (fmt == FMT_DF) reinterpret_cast<float4*>(p)[i] = v;
-        else reinterpret_cast<double2*>(p)[i] = df_to_double2(v);
-    }
-};
 
 // ------------------------------------------------------------ one pass ----
 
@@ -84,9 +42,11 @@ __device__ __forceinline__ void radix_pass(const typename A::C* src, typename A:
 {
     using C = typename A::C;
     const int nbf = n / R;
+    // butterfly b = slot + u * slots -> (t, k) = (b / m, b % m), stepped without division
+    const int dt = slots / m, dk = slots - dt * m;
+    int t = slot / m, k = slot - t * m;
 #pragma unroll 2
     for (int b = slot; b < nbf; b += slots) {
-        const int t = b / m, k = b - t * m;
         C v[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) v[j] = src[((t + s * j) * m + k) * ld];
@@ -97,6 +57,8 @@ __device__ __forceinline__ void radix_pass(const typename A::C* src, typename A:
         Dft<A, R>::run(v);
 #pragma unroll
         for (int q = 0; q < R; ++q) dst[(t * m * R + k + m * q) * ld] = v[q];
+        t += dt; k += dk;
+        if (k >= m) { k -= m; ++t; }
     }
     __syncthreads();
 }
@@ -128,14 +90,38 @@ fft_stage_kernel(const StageArgs p)
     }
     __syncthreads();
 
-    // (1) lines -> shared memory
+    // (1) lines -> shared memory: every element is one asynchronous copy, so
+    // all of the CTA's loads are in flight at once; format conversion and
+    // conjugation follow in place, by the thread that issued the copy.
     const int total = G * n;
-    for (int e = tid; e < total; e += kStageThreads) {
-        const int g = e / n, i = e - g * n;
-        const int64_t base = s_in[g];
-        C v = base >= 0 ? Io<A>::load(p.in, p.in_fmt, base + i) : A::zero();
-        if (p.conj_in) v = A::conj(v);
-        buf0[i * ld + g] = v;
+    {
+        constexpr int EB = sizeof(C) >= 16 ? 16 : 8;       // bytes copied per element
+        const char* src = reinterpret_cast<const char*>(p.in);
+        const int dg = kStageThreads / n, di = kStageThreads - dg * n;
+        int g = tid / n, i = tid - g * n;
+        for (int e = tid; e < total; e += kStageThreads) {
+            const int64_t base = s_in[g];
+            C* dst = buf0 + i * ld + g;
+            if (base >= 0) cp_async<EB>(dst, src + (base + i) * EB);
+            else *dst = A::zero();
+            i += di; g += dg;
+            if (i >= n) { i -= n; ++g; }
+        }
+        cp_async_wait_all();
+        const bool convert = sizeof(C) == 16 && p.in_fmt == FMT_C128 && EB == 16 && !std::is_same<A, ArF64>::value;
+        if (convert || p.conj_in) {
+            g = tid / n; i = tid - g * n;
+            for (int e = tid; e < total; e += kStageThreads) {
+                C* dst = buf0 + i * ld + g;
+                C v;
+                if (convert) v = Io<A>::from_c128(*reinterpret_cast<const double2*>(dst));
+                else v = *dst;
+                if (p.conj_in) v = A::conj(v);
+                *dst = v;
+                i += di; g += dg;
+                if (i >= n) { i -= n; ++g; }
+            }
+        }
     }
     __syncthreads();
 
@@ -167,14 +153,18 @@ fft_stage_kernel(const StageArgs p)
     // (3) shared memory -> next ordering
     const bool scale = p.scale != 1.0;
     if (p.contig_store) {
+        const int dg = kStageThreads / n, di = kStageThreads - dg * n;
+        int g = tid / n, k = tid - g * n;
         for (int e = tid; e < total; e += kStageThreads) {
-            const int g = e / n, k = e - g * n;
             const int64_t base = s_out[g];
-            if (base < 0) continue;
-            C v = cur[k * ld + g];
-            if (p.conj_out) v = A::conj(v);
-            if (scale) v = A::scale(v, p.scale);
-            Io<A>::store(p.out, p.out_fmt, base + k * p.Sk, v);
+            if (base >= 0) {
+                C v = cur[k * ld + g];
+                if (p.conj_out) v = A::conj(v);
+                if (scale) v = A::scale(v, p.scale);
+                Io<A>::store(p.out, p.out_fmt, base + k * p.Sk, v);
+            }
+            k += di; g += dg;
+            if (k >= n) { k -= n; ++g; }
         }
     } else {
         for (int e = tid; e < total; e += kStageThreads) {
@@ -222,6 +212,16 @@ cudaError_t stage_kernels_init(int max_dyn_smem)
 
 cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st)
 {
+    bool handled = false;
+    cudaError_t e = cudaSuccess;
+    if (L.args.do_fft) {
+        switch (L.arith) {
+        case ARITH_F64: e = launch_tile_f64(L, st, &handled); break;
+        case ARITH_F32: e = launch_tile_f32(L, st, &handled); break;
+        default: e = launch_tile_df(L, st, &handled); break;
+        }
+        if (handled || e) return e;
+    }
     const unsigned grid = (unsigned)L.grid;
     switch (L.arith) {
     case ARITH_F64: fft_stage_kernel<ArF64><<<grid, kStageThreads, L.smem, st>>>(L.args); break;

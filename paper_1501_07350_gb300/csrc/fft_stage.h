@@ -38,11 +38,16 @@ struct StageArgs {
 struct StageLaunch {
     StageArgs args;
     int arith;
-    int64_t grid;
-    size_t smem;
+    int64_t grid;              // CTAs of the generic kernel = tiles of G lines
+    size_t smem;               // dynamic shared memory of the generic kernel
+    int sms;                   // multiprocessors of the device (persistent grids)
 };
 
 cudaError_t stage_kernels_init(int max_dyn_smem);
+// specialised kernels (fft_tile_*.cu); *handled = false when (n, G) has none
+cudaError_t launch_tile_f64(const StageLaunch& L, cudaStream_t st, bool* handled);
+cudaError_t launch_tile_f32(const StageLaunch& L, cudaStream_t st, bool* handled);
+cudaError_t launch_tile_df(const StageLaunch& L, cudaStream_t st, bool* handled);
 cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st);
 cudaError_t launch_twiddles(int n, int fmt, void* out, cudaStream_t st);
 

@@ -1,0 +1,161 @@
+// stage_io.cuh -- element loads/stores of the stage kernels: global formats
+// (complex128, complex64, double-float pairs), the conversions between
+// double and double-float, and asynchronous global->shared copies.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "arith.cuh"
+#include "fft_stage.h"
+
+namespace ofg {
+
+// ------------------------------------------------ element load / store ----
+
+template <class A> struct Io;
+
+template <> struct Io<ArF64> {
+    static constexpr bool kConverts = false;
+    static constexpr int kExtBytes = 16, kMidBytes = 16;
+    __device__ __forceinline__ static void store_ext(void* p, double2 v) { *reinterpret_cast<double2*>(p) = v; }
+    __device__ __forceinline__ static void store_mid(void* p, double2 v) { *reinterpret_cast<double2*>(p) = v; }
+    __device__ __forceinline__ static double2 from_c128(double2 v) { return v; }
+    __device__ __forceinline__ static double2 load(const void* p, int, int64_t i) {
+        return __ldg(reinterpret_cast<const double2*>(p) + i);
+    }
+    __device__ __forceinline__ static void store(void* p, int, int64_t i, double2 v) {
+        reinterpret_cast<double2*>(p)[i] = v;
+    }
+};
+
+template <> struct Io<ArF32> {
+    static constexpr bool kConverts = false;
+    static constexpr int kExtBytes = 8, kMidBytes = 8;
+    __device__ __forceinline__ static void store_ext(void* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+    __device__ __forceinline__ static void store_mid(void* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+    __device__ __forceinline__ static float2 from_c128(double2 v) { return make_float2((float)v.x, (float)v.y); }
+    __device__ __forceinline__ static float2 load(const void* p, int, int64_t i) {
+        return __ldg(reinterpret_cast<const float2*>(p) + i);
+    }
+    __device__ __forceinline__ static void store(void* p, int, int64_t i, float2 v) {
+        reinterpret_cast<float2*>(p)[i] = v;
+    }
+};
+
+// Double-float: external arrays hold complex128; intermediate arrays hold the
+// (hi, lo) pairs themselves (FMT_DF), so conversions happen once on entry and
+// once on exit of the 3-D transform.  Both conversions use integer and FP32
+// instructions only (the FP64 and conversion units are slow on this part).
+
+// d -> (h, r): h keeps the sign, exponent and leading 24 significant bits of
+// d (truncated), r the next 23 bits, so |d - h - r| <= 2^-47 |d|.
+// |d| < 2^-126 is flushed to zero; r is dropped below 2^-103.
+__device__ __forceinline__ float2 split_f64(double d)
+{
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(d);
+    const uint32_t hw = (uint32_t)(bits >> 32), lw = (uint32_t)bits;
+    const uint32_t sign = hw & 0x80000000u;
+    const int e = (int)((hw >> 20) & 0x7FFu);              // biased double exponent
+    const int fe = e - 1023 + 127;                          // biased float exponent of h
+    if (fe <= 0) return make_float2(__uint_as_float(sign), 0.f);
+    if (fe >= 255) {                                        // too large for a float, inf, nan
+        const bool nan = e == 0x7FF && (((hw & 0xFFFFFu) | lw) != 0);
+        return make_float2(__uint_as_float(sign | 0x7F800000u | (nan ? 0x400000u : 0u)), 0.f);
+    }
+    const float h = __uint_as_float(sign | ((uint32_t)fe << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
+    // the low 29 fraction bits are worth (lw & 0x1FFFFFFF) * 2^(e-1075); their
+    // top 23 bits form the fraction of F = (1 + m 2^-23) 2^(xe-127), and
+    // F - 2^(xe-127) (exact) is their value.
+    const int xe = e - 919;
+    float r = 0.f;
+    if (xe >= 1) {
+        const float F = __uint_as_float(sign | ((uint32_t)xe << 23) | ((lw & 0x1FFFFFFFu) >> 6));
+        const float Pw = __uint_as_float(sign | ((uint32_t)xe << 23));
+        r = __fsub_rn(F, Pw);
+    }
+    return make_float2(h, r);
+}
+
+// (h, l) -> double of h + l, truncated toward the float significand of the
+// renormalised hi part: TwoSum gives s + e = h + l with |e| <= ulp(s)/2; the
+// double takes s's sign, exponent and 24-bit significand and adds e, scaled
+// to the double's last place, into the low 29 bits (a 64-bit add on two
+// 32-bit words).  A borrow below 2^52 (s a power of two, e < 0) lowers the
+// exponent by one.
+__device__ __forceinline__ double join_f64(float h, float l)
+{
+    float s, e;
+    ArDF::two_sum(h, l, s, e);
+    const uint32_t sb = __float_as_uint(s);
+    const uint32_t sign = sb & 0x80000000u;
+    const int es = (int)((sb >> 23) & 0xFFu);
+    if (es == 0 || es == 255) {                    // zero / tiny, inf / nan
+        const uint32_t hw = sign | (es == 255 ? (0x7FF00000u | ((sb & 0x7FFFFFu) ? 0x80000u : 0u)) : 0u);
+        return __hiloint2double((int)hw, 0);
+    }
+    const uint32_t man = sb & 0x7FFFFFu;
+    const uint32_t eb = __float_as_uint(e);
+    const int ee = (int)((eb >> 23) & 0xFFu);
+    int32_t d = 0;                                  // e in units of 2^(es-127-52), |d| < 2^29
+    if (ee != 0) {
+        const int32_t me = (int32_t)((1u << 23) | (eb & 0x7FFFFFu));
+        const int sh = ee - es + 29;
+        d = sh >= 0 ? (me << sh) : (sh > -31 ? (me >> -sh) : 0);
+        if ((eb ^ sb) & 0x80000000u) d = -d;
+    }
+    // significand (1 << 52 | man << 29) + d as (hi21:lo32)
+    unsigned long long M = ((unsigned long long)((1u << 20) | (man >> 3)) << 32) | (man << 29);
+    M += (unsigned long long)(long long)d;
+    int E = es + 896;                               // es - 127 + 1023
+    if (!(M >> 52)) { M <<= 1; E -= 1; }
+    const uint32_t hw = sign | ((uint32_t)E << 20) | ((uint32_t)(M >> 32) & 0xFFFFFu);
+    return __hiloint2double((int)hw, (int)(uint32_t)M);
+}
+
+__device__ __forceinline__ float4 df_from_double2(double2 v) {
+    const float2 r = split_f64(v.x), i = split_f64(v.y);
+    return make_float4(r.x, i.x, r.y, i.y);
+}
+__device__ __forceinline__ double2 df_to_double2(float4 v) {
+    return make_double2(join_f64(v.x, v.z), join_f64(v.y, v.w));
+}
+
+template <> struct Io<ArDF> {
+    static constexpr bool kConverts = true;
+    static constexpr int kExtBytes = 16, kMidBytes = 16;
+    __device__ __forceinline__ static void store_ext(void* p, float4 v) { *reinterpret_cast<double2*>(p) = df_to_double2(v); }
+    __device__ __forceinline__ static void store_mid(void* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+    __device__ __forceinline__ static float4 from_c128(double2 v) { return df_from_double2(v); }
+    __device__ __forceinline__ static float4 load(const void* p, int fmt, int64_t i) {
+        if (fmt == FMT_DF) return __ldg(reinterpret_cast<const float4*>(p) + i);
+        return df_from_double2(__ldg(reinterpret_cast<const double2*>(p) + i));
+    }
+    __device__ __forceinline__ static void store(void* p, int fmt, int64_t i, float4 v) {
+        if (fmt == FMT_DF) reinterpret_cast<float4*>(p)[i] = v;
+        else reinterpret_cast<double2*>(p)[i] = df_to_double2(v);
+    }
+};
+
+// -------------------------------------------------- asynchronous copies ----
+
+// global -> shared copy of one element that bypasses registers (cp.async).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem_dst, const void* gmem_src)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    if (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+// wait for all of this thread's outstanding copies
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
+}
+
+}  // namespace ofg

@@ -215,6 +215,31 @@ def test_512cubed_sampled(torch):
         of.openfft_destroy(plan)
 
 
+# ---------------------------------------- double-float value range ------
+
+@pytest.mark.parametrize("scale", [1e-25, 1e-8, 1.0, 3e7, 1e22])
+def test_double_float_range(torch, scale):
+    """The double-float arithmetic keeps FP64 accuracy across its documented
+    input range (|x| in [2^-100, 2^90]), including mixed magnitudes."""
+    Na, Nb, Nc = 24, 40, 30
+    x = synth.complex_field((Na, Nb, Nc), seed=13) * scale
+    x.reshape(-1)[::7] *= 1e-6          # a spread of exponents inside one array
+    ref = oracle.fft3d(x, Na, Nb, Nc, 6, oracle.FORWARD)
+    plan = of.openfft_plan(Na, Nb, Nc, 6, of.C2C_F64)
+    try:
+        for c in _all_candidates(plan):
+            cand = of.openfft_candidate(plan, c)
+            if cand["arith"] != of.ARITH_DOUBLE_FLOAT:
+                continue
+            of.openfft_set_tuning(plan, of.TUNE_USER, c)
+            y = _run(torch, plan, x, of.FORWARD, of.C2C_F64)
+            assert oracle.rel_l2(y, ref) < TOL_F64, (scale, cand)
+            z = _run(torch, plan, y, of.BACKWARD, of.C2C_F64)
+            assert oracle.rel_l2(z, x.reshape(-1)) < TOL_F64, (scale, cand)
+    finally:
+        of.openfft_destroy(plan)
+
+
 # ------------------------------------------------------------ errors ----
 
 def test_argument_errors(torch):
