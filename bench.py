@@ -232,7 +232,7 @@ def run_ours(args, rank, world, local_rank):
     traffic = profiled_traffic(khash)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": "fft_stage_kernel", "peak_kind": peak_kind,
+                "kernel": "FFT stage kernel (chosen family)", "peak_kind": peak_kind,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_us": round(avg_s * 1e6, 2),
                 "share_of_step": round(fft_ms / max(1e-9, phases["exec"]["ms"]), 4)}
 
@@ -316,16 +316,17 @@ def measure_forms(of, torch, plans_f64, x, y, z, n, stream, args):
             continue
         of.openfft_set_tuning(h, of.TUNE_USER, ci)
         ms = time_exec(h, x, y, of.FORWARD)
-        key = "f64_%s_G%d" % ("native" if c["arith"] == of.ARITH_NATIVE else "doublefloat", c["lines_per_cta"])
+        key = "f64_%s_G%d_%s" % ("native" if c["arith"] == of.ARITH_NATIVE else "doublefloat", c["lines_per_cta"],
+                                 ["auto", "warp", "tile", "generic"][c["kernel"]])
         out[key] = {"ms": round(ms, 4), "gflops": round(flops(N) / ms / 1e6, 1),
                     "hbm_frac": round(6 * N * 16 / (ms * 1e-3) / 1e9 / load_peaks()[0], 4)}
     for vi, name in [(of.VARIANT_PACK_UNPACK, "V1"), (of.VARIANT_PACK_EXCHANGE_UNPACK, "V0")]:
         for ci in range(of.openfft_num_candidates(h)):
             c = of.openfft_candidate(h, ci)
-            if c["variant"] == vi and c["lines_per_cta"] == 8 and c["arith"] == of.ARITH_NATIVE:
+            if c["variant"] == vi and c["arith"] == of.ARITH_DOUBLE_FLOAT:
                 of.openfft_set_tuning(h, of.TUNE_USER, ci)
                 ms = time_exec(h, x, y, of.FORWARD)
-                out["f64_native_%s" % name] = {"ms": round(ms, 4), "gflops": round(flops(N) / ms / 1e6, 1)}
+                out["f64_doublefloat_%s" % name] = {"ms": round(ms, 4), "gflops": round(flops(N) / ms / 1e6, 1)}
     of.openfft_set_tuning(h, of.TUNE_USER, cur)
     # FP32 form (complex64), auto-tuned
     x32 = x.to(torch.complex64)
@@ -419,8 +420,8 @@ def run_single(args, local_rank):
     _build.build()
     torch.cuda.set_device(local_rank)
     stream = torch.cuda.current_stream()
-    n = args.n
-    N = n ** 3
+    shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else (args.n,) * 3
+    N = shape[0] * shape[1] * shape[2]
     dtype = of.C2C_F32 if args.form == "f32" else of.C2C_F64
     want_arith = of.ARITH_DOUBLE_FLOAT if args.form == "f64-df" else of.ARITH_NATIVE
     want_variant = {"fused": of.VARIANT_FUSED, "v1": of.VARIANT_PACK_UNPACK,
@@ -429,12 +430,14 @@ def run_single(args, local_rank):
     if dtype == of.C2C_F32:
         x = x.to(torch.complex64)
     y = torch.empty_like(x)
-    h = of.openfft_plan(n, n, n, args.P, dtype)
+    h = of.openfft_plan(shape[0], shape[1], shape[2], args.P, dtype)
     of.openfft_set_stream(h, stream)
     pick = None
     for ci in range(of.openfft_num_candidates(h)):
         c = of.openfft_candidate(h, ci)
-        if c["variant"] == want_variant and c["arith"] == want_arith and c["lines_per_cta"] == args.G:
+        if (c["variant"] == want_variant and c["arith"] == want_arith and c["lines_per_cta"] == args.G
+                and (want_variant != of.VARIANT_FUSED
+                     or c["kernel"] == {"auto": 0, "warp": 0, "tile": 2, "generic": 3}[args.kernel])):
             pick = ci
     if pick is None:
         raise SystemExit("no such candidate")
@@ -451,7 +454,8 @@ def run_single(args, local_rank):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     E = 8 if dtype == of.C2C_F32 else 16
-    print(json.dumps({"single": args.form, "n": n, "P": args.P, "variant": args.variant, "G": args.G,
+    print(json.dumps({"single": args.form, "shape": list(shape), "P": args.P, "variant": args.variant,
+                      "G": args.G, "kernel": args.kernel,
                       "ms": round(ms, 4), "gflops": round(flops(N) / ms / 1e6, 1),
                       "hbm_frac": round(6 * N * E / (ms * 1e-3) / 1e9 / load_peaks()[0], 4)}))
     of.openfft_destroy(h)
@@ -472,8 +476,10 @@ def main():
     ap.add_argument("--form", choices=["f64-native", "f64-df", "f32"], default="f64-df")
     ap.add_argument("--variant", choices=["fused", "v1", "v0"], default="fused")
     ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--shape", default="", help="Na,Nb,Nc (overrides --n)")
     ap.add_argument("--P", type=int, default=64)
     ap.add_argument("--G", type=int, default=8)
+    ap.add_argument("--kernel", choices=["auto", "warp", "tile", "generic"], default="auto")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)     # at least 3 warm-up steps; the count run is reported
     rank = int(os.environ.get("RANK", "0"))

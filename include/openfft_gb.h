@@ -171,11 +171,17 @@ int openfft_decomp_degree(int Na, int Nb, int Nc, int P, int layout);
  * 2 runs per method) and keeps the fastest. */
 int openfft_set_tuning(openfft_plan_t plan, int mode, int candidate);
 
+/* Stage-kernel families: one warp per line (power-of-two lengths), tiles of
+ * lines specialised per length, or the generic kernel (any length); AUTO
+ * takes the first of these that exists for the length. */
+enum { OPENFFT_KERNEL_AUTO = 0, OPENFFT_KERNEL_WARP = 1, OPENFFT_KERNEL_TILE = 2, OPENFFT_KERNEL_GENERIC = 3 };
+
 /* Number of execution candidates of this plan and a description of one
- * (redistribution variant, arithmetic, lines per CTA, threads per CTA). */
+ * (redistribution variant, arithmetic, lines per CTA, kernel family).
+ * Candidate 0 is the default (OPENFFT_TUNE_DEFAULT). */
 int openfft_num_candidates(openfft_plan_t plan);
 int openfft_candidate(openfft_plan_t plan, int index, int* variant, int* arith,
-                      int* lines_per_cta, int* threads);
+                      int* lines_per_cta, int* kernel);
 /* Index of the candidate exec currently uses. */
 int openfft_current_candidate(openfft_plan_t plan);
 

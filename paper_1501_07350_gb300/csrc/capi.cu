@@ -61,6 +61,7 @@ struct Candidate {
     int variant;   // OPENFFT_VARIANT_*
     int arith;     // ARITH_*
     int G;         // lines per CTA target (power of two)
+    int family;    // KERNEL_*
 };
 
 // one step of an execution
@@ -119,7 +120,7 @@ int elem_bytes_of(int arith) { return arith == ARITH_F32 ? 8 : 16; }
 
 // Build the launch of one stage: lines of length n; l = i1 + i2*M1;
 // out(l,k) = i1*S1 + i2*S2 + k*Sk.
-int make_stage(openfft_plan_s* p, int axis, int arith, int Gt, int64_t M1, int64_t M2,
+int make_stage(openfft_plan_s* p, int axis, int arith, int Gt, int family, int64_t M1, int64_t M2,
                int64_t S1, int64_t S2, int64_t Sk, int group_i2, int contig, int in_fmt,
                int out_fmt, int conj_in, int conj_out, double scale, int do_fft, StageLaunch& L)
 {
@@ -148,6 +149,7 @@ int make_stage(openfft_plan_s* p, int axis, int arith, int Gt, int64_t M1, int64
     a.in_fmt = in_fmt; a.out_fmt = out_fmt;
     L.arith = arith;
     L.sms = p->sms;
+    L.family = family;
     L.grid = a.ngroups * (group_i2 ? M1 : M2);
     L.smem = 2 * (size_t)n * (G + 1) * E;     // two ping-pong tiles
     if (L.grid > 0x7fffffffLL) return fail(OPENFFT_ERR_UNSUPPORTED, "grid too large");
@@ -183,19 +185,19 @@ int build_ops(openfft_plan_s* p, const Candidate& c)
     int st;
     if (c.variant == OPENFFT_VARIANT_FUSED) {
         // forward: c-lines of abc -> cab; b-lines of cab -> cba; a-lines of cba in place
-        if ((st = make_stage(p, 2, ar, c.G, Na * Nb, 1, 1, 0, Na * Nb, 0, 0, ext, mid, 0, 0, 1.0, 1, L))) return st;
+        if ((st = make_stage(p, 2, ar, c.G, c.family, Na * Nb, 1, 1, 0, Na * Nb, 0, 0, ext, mid, 0, 0, 1.0, 1, L))) return st;
         F.push_back(stage_op(B_IN, B_A, L));
-        if ((st = make_stage(p, 1, ar, c.G, Na, Nc, 1, Nb * Na, Na, 0, 0, mid, mid, 0, 0, 1.0, 1, L))) return st;
+        if ((st = make_stage(p, 1, ar, c.G, c.family, Na, Nc, 1, Nb * Na, Na, 0, 0, mid, mid, 0, 0, 1.0, 1, L))) return st;
         F.push_back(stage_op(B_A, B_OUT, L));
-        if ((st = make_stage(p, 0, ar, c.G, Nc * Nb, 1, Na, 0, 1, 0, 1, mid, ext, 0, 0, 1.0, 1, L))) return st;
+        if ((st = make_stage(p, 0, ar, c.G, c.family, Nc * Nb, 1, Na, 0, 1, 0, 1, mid, ext, 0, 0, 1.0, 1, L))) return st;
         F.push_back(stage_op(B_OUT, B_OUT, L));
         // backward (conjugate on entry and exit): a-lines of cba -> cab; b-lines
         // of cab -> abc (grouped along c, whose output stride is 1); c-lines in place
-        if ((st = make_stage(p, 0, ar, c.G, Nb, Nc, 1, Na * Nb, Nb, 0, 0, ext, mid, 1, 0, 1.0, 1, L))) return st;
+        if ((st = make_stage(p, 0, ar, c.G, c.family, Nb, Nc, 1, Na * Nb, Nb, 0, 0, ext, mid, 1, 0, 1.0, 1, L))) return st;
         B.push_back(stage_op(B_IN, B_A, L));
-        if ((st = make_stage(p, 1, ar, c.G, Na, Nc, Nb * Nc, 1, Nc, 1, 0, mid, mid, 0, 0, 1.0, 1, L))) return st;
+        if ((st = make_stage(p, 1, ar, c.G, c.family, Na, Nc, Nb * Nc, 1, Nc, 1, 0, mid, mid, 0, 0, 1.0, 1, L))) return st;
         B.push_back(stage_op(B_A, B_OUT, L));
-        if ((st = make_stage(p, 2, ar, c.G, Na * Nb, 1, Nc, 0, 1, 0, 1, mid, ext, 0, 1, invN, 1, L))) return st;
+        if ((st = make_stage(p, 2, ar, c.G, c.family, Na * Nb, 1, Nc, 0, 1, 0, 1, mid, ext, 0, 1, invN, 1, L))) return st;
         B.push_back(stage_op(B_OUT, B_OUT, L));
         return OPENFFT_OK;
     }
@@ -220,22 +222,22 @@ int build_ops(openfft_plan_s* p, const Candidate& c)
     };
     auto other_of = [](int b) { return b == B_A ? B_B : B_A; };
     // forward
-    if ((st = make_stage(p, 2, ar, c.G, Na * Nb, 1, Nc, 0, 1, 0, 1, ext, mid, 0, 0, 1.0, 1, L))) return st;
+    if ((st = make_stage(p, 2, ar, c.G, c.family, Na * Nb, 1, Nc, 0, 1, 0, 1, ext, mid, 0, 0, 1.0, 1, L))) return st;
     F.push_back(stage_op(B_IN, B_A, L));
     int x = transpose(F, 0, B_A, -1);                // abc -> cab
-    if ((st = make_stage(p, 1, ar, c.G, Nc * Na, 1, Nb, 0, 1, 0, 1, mid, mid, 0, 0, 1.0, 1, L))) return st;
+    if ((st = make_stage(p, 1, ar, c.G, c.family, Nc * Na, 1, Nb, 0, 1, 0, 1, mid, mid, 0, 0, 1.0, 1, L))) return st;
     F.push_back(stage_op(x, other_of(x), L));
     transpose(F, 1, other_of(x), B_OUT);             // cab -> cba lands in out
-    if ((st = make_stage(p, 0, ar, c.G, Nc * Nb, 1, Na, 0, 1, 0, 1, mid, ext, 0, 0, 1.0, 1, L))) return st;
+    if ((st = make_stage(p, 0, ar, c.G, c.family, Nc * Nb, 1, Na, 0, 1, 0, 1, mid, ext, 0, 0, 1.0, 1, L))) return st;
     F.push_back(stage_op(B_OUT, B_OUT, L));
     // backward
-    if ((st = make_stage(p, 0, ar, c.G, Nc * Nb, 1, Na, 0, 1, 0, 1, ext, mid, 1, 0, 1.0, 1, L))) return st;
+    if ((st = make_stage(p, 0, ar, c.G, c.family, Nc * Nb, 1, Na, 0, 1, 0, 1, ext, mid, 1, 0, 1.0, 1, L))) return st;
     B.push_back(stage_op(B_IN, B_A, L));
     x = transpose(B, 2, B_A, -1);                    // cba -> cab
-    if ((st = make_stage(p, 1, ar, c.G, Nc * Na, 1, Nb, 0, 1, 0, 1, mid, mid, 0, 0, 1.0, 1, L))) return st;
+    if ((st = make_stage(p, 1, ar, c.G, c.family, Nc * Na, 1, Nb, 0, 1, 0, 1, mid, mid, 0, 0, 1.0, 1, L))) return st;
     B.push_back(stage_op(x, other_of(x), L));
     transpose(B, 3, other_of(x), B_OUT);             // cab -> abc lands in out
-    if ((st = make_stage(p, 2, ar, c.G, Na * Nb, 1, Nc, 0, 1, 0, 1, mid, ext, 0, 1, invN, 1, L))) return st;
+    if ((st = make_stage(p, 2, ar, c.G, c.family, Na * Nb, 1, Nc, 0, 1, 0, 1, mid, ext, 0, 1, invN, 1, L))) return st;
     B.push_back(stage_op(B_OUT, B_OUT, L));
     return OPENFFT_OK;
 }
@@ -468,15 +470,26 @@ openfft_plan_t openfft_plan(int Na, int Nb, int Nc, int P, int dtype)
         if (!ch.empty()) cudaMemcpy(T.d_chunks, ch.data(), ch.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
     }
     if ((e = cudaDeviceSynchronize())) { cuda_fail(e, "plan setup"); free_plan(p); return nullptr; }
-    // candidates: (variant, arithmetic, lines per CTA)
-    const int variants[3] = {OPENFFT_VARIANT_FUSED, OPENFFT_VARIANT_PACK_UNPACK, OPENFFT_VARIANT_PACK_EXCHANGE_UNPACK};
-    const int Gs[3] = {8, 16, 4};
-    std::vector<int> ariths;
-    if (dtype == OPENFFT_C2C_F32) ariths = {ARITH_F32};
-    else ariths = {ARITH_F64, ARITH_DF};
-    for (int v : variants)
-        for (int ar : ariths)
-            for (int g : Gs) p->cands.push_back(Candidate{v, ar, g});
+    // candidates (Sec. 3.2.3: the set the tuner chooses from).  The fused
+    // variant is tried with every stage-kernel family and tile width; the
+    // explicit variants V1 and V0 (the paper's pack / communicate / unpack
+    // methods) with the default kernel.  The first candidate is the default.
+    {
+        std::vector<int> ariths;
+        if (dtype == OPENFFT_C2C_F32) ariths = {ARITH_F32};
+        else ariths = {ARITH_DF, ARITH_F64};
+        const bool f32 = dtype == OPENFFT_C2C_F32;
+        const int gw = f32 ? 16 : 8, gn = f32 ? 8 : 4;
+        for (int ar : ariths) {
+            p->cands.push_back(Candidate{OPENFFT_VARIANT_FUSED, ar, gw, KERNEL_AUTO});
+            p->cands.push_back(Candidate{OPENFFT_VARIANT_FUSED, ar, gn, KERNEL_AUTO});
+            p->cands.push_back(Candidate{OPENFFT_VARIANT_FUSED, ar, gw, KERNEL_TILE});
+            p->cands.push_back(Candidate{OPENFFT_VARIANT_FUSED, ar, gn, KERNEL_TILE});
+            p->cands.push_back(Candidate{OPENFFT_VARIANT_FUSED, ar, gw, KERNEL_GENERIC});
+            p->cands.push_back(Candidate{OPENFFT_VARIANT_PACK_UNPACK, ar, gw, KERNEL_AUTO});
+            p->cands.push_back(Candidate{OPENFFT_VARIANT_PACK_EXCHANGE_UNPACK, ar, gw, KERNEL_AUTO});
+        }
+    }
     if (select_candidate(p, 0)) { free_plan(p); return nullptr; }
     return p;
 }
@@ -552,14 +565,14 @@ int openfft_counts(openfft_plan_t plan, int exchange, int64_t* PxP)
 
 int openfft_num_candidates(openfft_plan_t plan) { return plan ? (int)plan->cands.size() : 0; }
 
-int openfft_candidate(openfft_plan_t plan, int index, int* variant, int* arith, int* lines_per_cta, int* threads)
+int openfft_candidate(openfft_plan_t plan, int index, int* variant, int* arith, int* lines_per_cta, int* kernel)
 {
     if (!plan || index < 0 || index >= (int)plan->cands.size()) return fail(OPENFFT_ERR_INVALID_ARG, "bad candidate");
     const Candidate& c = plan->cands[(size_t)index];
     if (variant) *variant = c.variant;
     if (arith) *arith = c.arith == ARITH_DF ? OPENFFT_ARITH_DOUBLE_FLOAT : OPENFFT_ARITH_NATIVE;
     if (lines_per_cta) *lines_per_cta = c.G;
-    if (threads) *threads = kStageThreads;
+    if (kernel) *kernel = c.family;
     return OPENFFT_OK;
 }
 
@@ -656,10 +669,10 @@ int openfft_redistribute(openfft_plan_t plan, int exchange, int variant, const v
         StageLaunch L;
         int st;
         switch (exchange) {
-        case 1: st = make_stage(plan, 2, ar, 8, Na * Nb, 1, 1, 0, Na * Nb, 0, 0, fmt, fmt, 0, 0, 1.0, 0, L); break;
-        case 2: st = make_stage(plan, 1, ar, 8, Na, Nc, 1, Nb * Na, Na, 0, 0, fmt, fmt, 0, 0, 1.0, 0, L); break;
-        case -2: st = make_stage(plan, 0, ar, 8, Nb, Nc, 1, Na * Nb, Nb, 0, 0, fmt, fmt, 0, 0, 1.0, 0, L); break;
-        default: st = make_stage(plan, 1, ar, 8, Na, Nc, Nb * Nc, 1, Nc, 1, 0, fmt, fmt, 0, 0, 1.0, 0, L); break;
+        case 1: st = make_stage(plan, 2, ar, 8, KERNEL_GENERIC, Na * Nb, 1, 1, 0, Na * Nb, 0, 0, fmt, fmt, 0, 0, 1.0, 0, L); break;
+        case 2: st = make_stage(plan, 1, ar, 8, KERNEL_GENERIC, Na, Nc, 1, Nb * Na, Na, 0, 0, fmt, fmt, 0, 0, 1.0, 0, L); break;
+        case -2: st = make_stage(plan, 0, ar, 8, KERNEL_GENERIC, Nb, Nc, 1, Na * Nb, Nb, 0, 0, fmt, fmt, 0, 0, 1.0, 0, L); break;
+        default: st = make_stage(plan, 1, ar, 8, KERNEL_GENERIC, Na, Nc, Nb * Nc, 1, Nc, 1, 0, fmt, fmt, 0, 0, 1.0, 0, L); break;
         }
         if (st) return st;
         L.args.in = in; L.args.out = out;

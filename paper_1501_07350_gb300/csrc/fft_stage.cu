@@ -214,7 +214,7 @@ cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st)
 {
     bool handled = false;
     cudaError_t e = cudaSuccess;
-    if (L.args.do_fft) {
+    if (L.args.do_fft && L.family != KERNEL_GENERIC) {
         switch (L.arith) {
         case ARITH_F64: e = launch_tile_f64(L, st, &handled); break;
         case ARITH_F32: e = launch_tile_f32(L, st, &handled); break;

@@ -41,7 +41,12 @@ struct StageLaunch {
     int64_t grid;              // CTAs of the generic kernel = tiles of G lines
     size_t smem;               // dynamic shared memory of the generic kernel
     int sms;                   // multiprocessors of the device (persistent grids)
+    int family;                // KERNEL_*: which stage kernel runs this launch
 };
+
+// stage kernel families: warp-per-line (power-of-two n), tile (specialised n),
+// generic (any n); AUTO takes the first that has an instantiation for (n, G)
+enum { KERNEL_AUTO = 0, KERNEL_WARP = 1, KERNEL_TILE = 2, KERNEL_GENERIC = 3 };
 
 cudaError_t stage_kernels_init(int max_dyn_smem);
 // specialised kernels (fft_tile_*.cu); *handled = false when (n, G) has none

@@ -1,0 +1,275 @@
+// fft_warp.cuh -- FFT stage kernel for power-of-two line lengths (32..512):
+// one warp per line.  The radix passes of a line need only its own warp, so
+// they synchronise with __syncwarp; the CTA synchronises twice per tile, around
+// the store that gathers the G lines of the tile (the transposed store writes
+// G consecutive elements of the next ordering at each frequency).
+//
+// Per-warp line layout in shared memory: one padding element per 128 bytes
+// (element p at p + (p >> 3) for 16-byte elements, p + (p >> 4) for 8-byte
+// ones).  With the radix order "remainder radix (2 or 4) first, then radix 8"
+// every read (positions b + j N/R, b = lane + 32 u) and every write
+// (t m R + k + m q) of a Stockham pass is free of bank conflicts for 16-byte
+// elements and at most 2-way for 8-byte ones (checked for N = 32..512); lines
+// sit an odd number of elements apart, so the transposed store (consecutive
+// lanes = consecutive lines) is conflict-free too.
+//
+// The radix pass is the same Stockham decimation-in-time step as in
+// fft_stage.cu; in-place in the warp's line with a __syncwarp between reads
+// and writes.  Tiles are processed persistently; the next tile's lines are
+// copied (cp.async) while the current tile is transformed.
+#pragma once
+#include "arith.cuh"
+#include "fft_stage.h"
+#include "fft_tile.cuh"
+#include "stage_io.cuh"
+
+namespace ofg {
+
+constexpr int wplan_len(int n)
+{
+    int c = 0;
+    while (n % 8 == 0) { n /= 8; ++c; }
+    return c + (n > 1 ? 1 : 0);
+}
+
+// remainder radix (N / 8^k, which is 1, 2 or 4) first, then radix 8
+constexpr int wplan_radix(int n, int idx)
+{
+    int k = 0, r = n;
+    while (r % 8 == 0) { r /= 8; ++k; }
+    if (r > 1) return idx == 0 ? r : 8;
+    return 8;
+}
+
+constexpr int wplan_m(int n, int idx)
+{
+    int m = 1;
+    for (int i = 0; i < idx; ++i) m *= wplan_radix(n, i);
+    return m;
+}
+
+// one padding element per 128 bytes of line: per 8 elements of 16 bytes,
+// per 16 elements of 8 bytes
+template <int EB>
+__host__ __device__ constexpr int wpad(int p) { return p + (p >> (EB >= 16 ? 3 : 4)); }
+
+// shared-memory stride between lines: odd, at least the padded length
+template <int EB>
+constexpr int warp_line_stride(int N) { return (wpad<EB>(N - 1) + 1) | 1; }
+
+template <class A, int N>
+struct WarpLine {
+    using C = typename A::C;
+    using W = typename A::W;
+    static constexpr int kPasses = wplan_len(N);
+    static constexpr int EB = sizeof(C);
+
+    template <int P>
+    __device__ __forceinline__ static void pass(C* line, const W* __restrict__ tw, int lane)
+    {
+        constexpr int R = wplan_radix(N, P);
+        constexpr int m = wplan_m(N, P);
+        constexpr int s = N / (m * R);
+        constexpr int NBF = N / R;
+        constexpr int NB = (NBF + 31) / 32;
+        C v[NB][R];
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int b = lane + 32 * u;
+            if (NBF % 32 == 0 || b < NBF) {
+#pragma unroll
+                for (int j = 0; j < R; ++j) v[u][j] = line[wpad<EB>(b + j * NBF)];
+                if (m > 1) {
+                    const int k = b % m;
+                    const int ks = k * s;
+#pragma unroll
+                    for (int j = 1; j < R; ++j) v[u][j] = A::mul(v[u][j], __ldg(tw + j * ks));
+                }
+                Dft<A, R>::run(v[u]);
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int b = lane + 32 * u;
+            if (NBF % 32 == 0 || b < NBF) {
+                const int t = b / m, k = b % m;
+                const int base = t * m * R + k;
+#pragma unroll
+                for (int q = 0; q < R; ++q) line[wpad<EB>(base + m * q)] = v[u][q];
+            }
+        }
+        __syncwarp();
+    }
+
+    template <int P>
+    __device__ __forceinline__ static void passes(C* line, const W* __restrict__ tw, int lane)
+    {
+        if constexpr (P < kPasses) {
+            pass<P>(line, tw, lane);
+            passes<P + 1>(line, tw, lane);
+        }
+    }
+};
+
+// copies of line g (= warp) of a tile
+template <class A, int N>
+__device__ __forceinline__ void warp_issue_load(const StageArgs& p, const TileGeom& tg, int g,
+                                                typename A::C* line, int lane)
+{
+    constexpr int EB = sizeof(typename A::C) >= 16 ? 16 : 8;
+    if (g < tg.valid) {
+        const char* src = reinterpret_cast<const char*>(p.in) + (tg.line0 + g * tg.lstride) * (int64_t)(N * EB);
+#pragma unroll
+        for (int u = 0; u < N / 32; ++u) {
+            const int pos = lane + 32 * u;
+            cp_async<EB>(line + wpad<sizeof(typename A::C)>(pos), src + pos * EB);
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < N / 32; ++u) line[wpad<sizeof(typename A::C)>(lane + 32 * u)] = A::zero();
+    }
+    cp_async_commit();
+}
+
+template <class A, int N, bool CONVERT, bool CONJ>
+__device__ __forceinline__ void warp_fix(typename A::C* line, int lane)
+{
+    using C = typename A::C;
+#pragma unroll
+    for (int u = 0; u < N / 32; ++u) {
+        C* x = line + wpad<sizeof(C)>(lane + 32 * u);
+        C v;
+        if constexpr (CONVERT) v = Io<A>::from_c128(*reinterpret_cast<const double2*>(x));
+        else v = *x;
+        if constexpr (CONJ) v = A::conj(v);
+        *x = v;
+    }
+}
+
+template <class A, int N, int G, bool CONTIG, bool CONJ_SCALE, bool EXT>
+__device__ __forceinline__ void warp_tile_store(const StageArgs& p, const TileGeom& tg,
+                                                const typename A::C* buf, int tid)
+{
+    constexpr int CB = sizeof(typename A::C);
+    constexpr int LS = warp_line_stride<CB>(N);
+    constexpr int EB = EXT ? Io<A>::kExtBytes : Io<A>::kMidBytes;
+    char* first = reinterpret_cast<char*>(p.out) + tg.obase * EB;
+    if constexpr (!CONTIG) {
+        // thread (g, slot): line g, frequencies slot, slot + 32, ...
+        const int g = tid % G, slot = tid / G;
+        if (g >= tg.valid) return;
+        const typename A::C* line = buf + g * LS;
+        char* ptr = first + (g * tg.ostride + slot * p.Sk) * EB;
+        const int64_t step = (int64_t)32 * p.Sk * EB;
+#pragma unroll 4
+        for (int k = slot; k < N; k += 32) {
+            put<A, CONJ_SCALE, EXT>(ptr, line[wpad<CB>(k)], p.scale);
+            ptr += step;
+        }
+    } else {
+        // warp g stores its own line, which is contiguous in the output
+        const int g = tid >> 5, lane = tid & 31;
+        if (g >= tg.valid) return;
+        const typename A::C* line = buf + g * LS;
+        char* ptr = first + (int64_t)g * tg.ostride * EB;
+#pragma unroll
+        for (int u = 0; u < N / 32; ++u) {
+            const int k = lane + 32 * u;
+            put<A, CONJ_SCALE, EXT>(ptr + k * EB, line[wpad<CB>(k)], p.scale);
+        }
+    }
+}
+
+template <class A, int N, int G>
+__device__ __forceinline__ void warp_store_dispatch(const StageArgs& p, const TileGeom& tg,
+                                                    const typename A::C* buf, int tid)
+{
+    const bool ext = p.out_fmt != FMT_DF;
+    const bool cs = p.conj_out != 0;
+    if (!p.contig_store) {
+        if (cs) { if (ext) warp_tile_store<A, N, G, false, true, true>(p, tg, buf, tid); else warp_tile_store<A, N, G, false, true, false>(p, tg, buf, tid); }
+        else    { if (ext) warp_tile_store<A, N, G, false, false, true>(p, tg, buf, tid); else warp_tile_store<A, N, G, false, false, false>(p, tg, buf, tid); }
+    } else {
+        if (cs) { if (ext) warp_tile_store<A, N, G, true, true, true>(p, tg, buf, tid); else warp_tile_store<A, N, G, true, true, false>(p, tg, buf, tid); }
+        else    { if (ext) warp_tile_store<A, N, G, true, false, true>(p, tg, buf, tid); else warp_tile_store<A, N, G, true, false, false>(p, tg, buf, tid); }
+    }
+}
+
+// register budget: 128 per thread for 16-byte elements, 64-80 for 8-byte ones
+constexpr int warp_min_blocks(int T, int EB) { return EB >= 16 ? (512 / T > 0 ? 512 / T : 1) : (T >= 512 ? 2 : 3); }
+
+template <class A, int N, int G>
+__global__ void __launch_bounds__(32 * G, warp_min_blocks(32 * G, sizeof(typename A::C)))
+fft_warp_kernel(const StageArgs p, int64_t ntiles)
+{
+    using C = typename A::C;
+    constexpr int LS = warp_line_stride<sizeof(C)>(N);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* cur = reinterpret_cast<C*>(smem_raw);
+    C* nxt = cur + G * LS;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const typename A::W* tw = reinterpret_cast<const typename A::W*>(p.tw);
+    const bool convert = Io<A>::kConverts && p.in_fmt == FMT_C128;
+
+    int64_t tile = blockIdx.x;
+    if (tile < ntiles) warp_issue_load<A, N>(p, tile_geom(p, tile, G), warp, cur + warp * LS, lane);
+    for (; tile < ntiles; tile += gridDim.x) {
+        const TileGeom tg = tile_geom(p, tile, G);
+        C* line = cur + warp * LS;
+        cp_async_wait_all();
+        if (convert) { if (p.conj_in) warp_fix<A, N, true, true>(line, lane); else warp_fix<A, N, true, false>(line, lane); }
+        else if (p.conj_in) warp_fix<A, N, false, true>(line, lane);
+        __syncwarp();
+        const int64_t next = tile + gridDim.x;
+        if (next < ntiles) warp_issue_load<A, N>(p, tile_geom(p, next, G), warp, nxt + warp * LS, lane);
+        WarpLine<A, N>::template passes<0>(line, tw, lane);
+        __syncthreads();                   // every line of the tile is transformed
+        warp_store_dispatch<A, N, G>(p, tg, cur, tid);
+        __syncthreads();                   // cur becomes the next prefetch target
+        C* t = cur; cur = nxt; nxt = t;
+    }
+    cp_async_wait_all();
+}
+
+template <class A, int N, int G>
+cudaError_t launch_warp_n(const StageLaunch& L, cudaStream_t st)
+{
+    constexpr int T = 32 * G;
+    const size_t smem = 2 * (size_t)G * warp_line_stride<sizeof(typename A::C)>(N) * sizeof(typename A::C);
+    static int blocks_per_sm = -1;
+    if (blocks_per_sm < 0) {
+        cudaError_t e = cudaFuncSetAttribute(fft_warp_kernel<A, N, G>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e) return e;
+        int b = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fft_warp_kernel<A, N, G>, T, smem);
+        if (e) return e;
+        blocks_per_sm = b > 0 ? b : 1;
+    }
+    const int64_t ntiles = L.grid;
+    int64_t grid = (int64_t)L.sms * blocks_per_sm;
+    if (grid > ntiles) grid = ntiles;
+    if (grid < 1) grid = 1;
+    fft_warp_kernel<A, N, G><<<(unsigned)grid, T, smem, st>>>(L.args, ntiles);
+    return cudaGetLastError();
+}
+
+// power-of-two lengths go to the warp-per-line kernel
+template <class A, int G>
+cudaError_t launch_warp_g(const StageLaunch& L, cudaStream_t st, bool* handled)
+{
+    const StageArgs& a = L.args;
+    if (a.contig_store && (a.group_i2 || a.S1 != a.n || a.Sk != 1)) { *handled = false; return cudaSuccess; }
+    *handled = true;
+    switch (a.n) {
+    case 32: return launch_warp_n<A, 32, G>(L, st);
+    case 64: return launch_warp_n<A, 64, G>(L, st);
+    case 128: return launch_warp_n<A, 128, G>(L, st);
+    case 256: return launch_warp_n<A, 256, G>(L, st);
+    case 512: return launch_warp_n<A, 512, G>(L, st);
+    default: *handled = false; return cudaSuccess;
+    }
+}
+
+}  // namespace ofg

@@ -26,6 +26,7 @@ VARIANT_PACK_EXCHANGE_UNPACK, VARIANT_PACK_UNPACK, VARIANT_FUSED = 0, 1, 2
 ARITH_NATIVE, ARITH_DOUBLE_FLOAT = 0, 1
 TUNE_DEFAULT, TUNE_EXHAUSTIVE, TUNE_LEARNED, TUNE_USER = 0, 1, 2, 3
 LAYOUT_ABC, LAYOUT_CAB, LAYOUT_CBA = 0, 1, 2
+KERNEL_AUTO, KERNEL_WARP, KERNEL_TILE, KERNEL_GENERIC = 0, 1, 2, 3
 
 # every symbol declared in include/openfft_gb.h
 EXPORTS = [
@@ -184,7 +185,7 @@ def openfft_num_candidates(plan: int) -> int:
 def openfft_candidate(plan: int, index: int):
     v, a, g, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(load().openfft_candidate(plan, index, ctypes.byref(v), ctypes.byref(a), ctypes.byref(g), ctypes.byref(t)))
-    return {"variant": v.value, "arith": a.value, "lines_per_cta": g.value, "threads": t.value}
+    return {"variant": v.value, "arith": a.value, "lines_per_cta": g.value, "kernel": t.value}
 
 
 def openfft_current_candidate(plan: int) -> int:
