@@ -208,6 +208,31 @@ int openfft_get_timing(openfft_plan_t plan, double ms[4], int64_t launches[4]);
 int openfft_redistribute(openfft_plan_t plan, int exchange, int variant,
                          const void* in, void* out);
 
+/* ------------------------------------------------- allocation-free ----- */
+
+/* The same transform as openfft_exec_c2c (fused variant, default arithmetic
+ * of the dtype), for callers that may not allocate device memory: it needs no
+ * plan and calls no cudaMalloc, cudaFree or allocating library routine, so it
+ * fits a host framework whose own allocator owns the device budget, or a code
+ * path that must not pay for the device synchronisation a cudaMalloc or
+ * cudaFree can imply.  The paper has no counterpart of this entry point.
+ *
+ * The caller passes device pointers `in` / `out` (N elements of complex128
+ * for OPENFFT_C2C_F64, complex64 for OPENFFT_C2C_F32, 16-byte aligned, in !=
+ * out) and a cudaStream_t `stream` (NULL = legacy default stream); P, the
+ * layouts and dir are as for openfft_plan / openfft_exec_c2c.  The
+ * intermediate array and twiddle tables live in a 16 MiB (+96 KiB) static
+ * device array that every GPU loading this library keeps until the process
+ * exits: N times the element size (16 or 8 bytes) must not exceed 16 MiB and
+ * no axis may exceed 2048, otherwise the call returns OPENFFT_ERR_UNSUPPORTED
+ * without touching the GPU.  The array's device address is looked up on the
+ * first call on each device (with that device current), so make that first
+ * call before any stream capture.  All calls share the array: calls whose
+ * kernels may overlap on the GPU (unordered streams) race and must be
+ * serialised by the caller.  Asynchronous on `stream`. */
+int openfft_exec_c2c_noalloc(int Na, int Nb, int Nc, int P, int dtype,
+                             const void* in, void* out, int dir, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

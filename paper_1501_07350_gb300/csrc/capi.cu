@@ -367,6 +367,11 @@ int box_of(const Ordering& o, int rank, int64_t start[3], int64_t end[3], int64_
 
 }  // namespace
 
+namespace ofg {
+// error reporting for entry points defined in other translation units
+int set_last_error(int status, const char* msg) { return fail(status, msg); }
+}  // namespace ofg
+
 // =================================================================== ABI ==
 
 extern "C" {

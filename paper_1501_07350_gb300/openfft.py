@@ -34,7 +34,7 @@ EXPORTS = [
     "openfft_set_stream", "openfft_last_error", "openfft_last_status", "openfft_box", "openfft_counts",
     "openfft_decomp_box", "openfft_decomp_counts", "openfft_decomp_degree", "openfft_set_tuning",
     "openfft_num_candidates", "openfft_candidate", "openfft_current_candidate", "openfft_redistribute",
-    "openfft_set_timing", "openfft_get_timing",
+    "openfft_set_timing", "openfft_get_timing", "openfft_exec_c2c_noalloc",
 ]
 
 _lock = threading.Lock()
@@ -86,6 +86,7 @@ def load():
             "openfft_redistribute": (i32, [vp, i32, i32, vp, vp]),
             "openfft_set_timing": (i32, [vp, i32]),
             "openfft_get_timing": (i32, [vp, ctypes.POINTER(ctypes.c_double), p64]),
+            "openfft_exec_c2c_noalloc": (i32, [i32, i32, i32, i32, i32, vp, vp, i32, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -209,6 +210,13 @@ def openfft_get_timing(plan: int) -> dict:
     n = (ctypes.c_int64 * 4)()
     _check(load().openfft_get_timing(plan, ms, n))
     return {name: {"ms": ms[i], "launches": n[i]} for i, name in enumerate(PHASES)}
+
+
+def openfft_exec_c2c_noalloc(Na: int, Nb: int, Nc: int, P: int, dtype: int, inp, out, direction: int,
+                             stream=None) -> None:
+    """Plan-free transform that allocates nothing (static device scratch, 16 MiB)."""
+    raw = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(load().openfft_exec_c2c_noalloc(Na, Nb, Nc, P, dtype, _ptr(inp), _ptr(out), direction, raw))
 
 
 # ------------------------------------------------------- convenience ----
