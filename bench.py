@@ -345,6 +345,11 @@ def measure_forms(of, torch, plans_f64, x, y, z, n, stream, args):
                   "chosen": of.openfft_candidate(h32, of.openfft_current_candidate(h32))}
     of.openfft_destroy(h32)
     del x32, y32
+    # batched: 64 uneven transforms (sizes drawn from {48^3, 64^3, 96^3, 100x108x120}),
+    # complex64, P = 8 each, one persistent graph launch -- against the same 64
+    # transforms run one plan at a time in FP64 and in FP32
+    if not args.no_batch:
+        out["batch64"] = measure_batch(of, torch, stream)
     # 512^3 forward, FP64, P = 1024 (the large configuration)
     if not args.no_512:
         n5 = 512
@@ -365,6 +370,77 @@ def measure_forms(of, torch, plans_f64, x, y, z, n, stream, args):
         del xb, yb
         torch.cuda.empty_cache()
     return out
+
+
+def measure_batch(of, torch, stream, count=64, reps=5):
+    from paper_1501_07350_gb300 import synth
+    shapes = synth.batch_shapes(synth.config_seed(4), count)
+    Ps = [8] * count
+    work = sum(flops(a * b * c) for a, b, c in shapes)
+    bytes64 = sum(48 * a * b * c for a, b, c in shapes)
+    xs = [torch.from_numpy(synth.complex_field((a * b * c,), seed=synth.config_seed(4) + 1 + i)).cuda()
+          for i, (a, b, c) in enumerate(shapes)]
+    x32 = [x.to(torch.complex64) for x in xs]
+    y32 = [torch.empty_like(x) for x in x32]
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    res = {"transforms": count, "points": int(sum(a * b * c for a, b, c in shapes)), "gflop": round(work / 1e9, 3)}
+    hb = of.openfft_plan_many(shapes, Ps, of.C2C_F32)
+    of.openfft_set_stream(hb, stream)
+    ms = timed(lambda: of.openfft_exec_many(hb, x32, y32, of.FORWARD))
+    of.openfft_sync(hb)
+    # accuracy of the batched form against the per-transform FP64 plans (checked below)
+    res["batched_c64_graph"] = {"ms": round(ms, 4), "gflops": round(work / ms / 1e6, 1),
+                                "hbm_frac": round(bytes64 / (ms * 1e-3) / 1e9 / load_peaks()[0], 4)}
+    plans64 = []
+    for (a, b, c) in shapes:
+        h = of.openfft_plan(a, b, c, 8, of.C2C_F64)
+        of.openfft_set_stream(h, stream)
+        of.openfft_set_tuning(h, of.TUNE_USER, [i for i in range(of.openfft_num_candidates(h))
+                                                if of.openfft_candidate(h, i)["arith"] == of.ARITH_NATIVE][0])
+        plans64.append(h)
+    y64 = [torch.empty_like(x) for x in xs]
+
+    def run64():
+        for h, x, y in zip(plans64, xs, y64):
+            of.openfft_exec_c2c(h, x, y, of.FORWARD)
+    ms64 = timed(run64)
+    res["per_transform_f64_native"] = {"ms": round(ms64, 4), "gflops": round(work / ms64 / 1e6, 1)}
+    errs = [float(torch.linalg.vector_norm(a.to(torch.complex128) - b) / torch.linalg.vector_norm(b))
+            for a, b in zip(y32, y64)]
+    res["batched_c64_graph"]["max_rel_l2_vs_f64"] = max(errs)
+    res["batched_c64_graph"]["bound"] = 1e-5
+    for h in plans64:
+        of.openfft_destroy(h)
+    plans32 = []
+    for (a, b, c) in shapes:
+        h = of.openfft_plan(a, b, c, 8, of.C2C_F32)
+        of.openfft_set_stream(h, stream)
+        plans32.append(h)
+
+    def run32():
+        for h, x, y in zip(plans32, x32, y32):
+            of.openfft_exec_c2c(h, x, y, of.FORWARD)
+    ms32 = timed(run32)
+    res["per_transform_c64"] = {"ms": round(ms32, 4), "gflops": round(work / ms32 / 1e6, 1)}
+    for h in plans32:
+        of.openfft_destroy(h)
+    of.openfft_destroy(hb)
+    return res
 
 
 def cpu_baseline_sample(x_np, n):
@@ -470,6 +546,8 @@ def main():
     ap.add_argument("--tune", choices=["exhaustive", "default"], default="exhaustive")
     ap.add_argument("--quick", action="store_true", help="skip the other forms")
     ap.add_argument("--no-512", dest="no_512", action="store_true", help="skip the 512^3 form")
+    ap.add_argument("--no-batch", dest="no_batch", action="store_true", help="skip the batched form")
+    ap.add_argument("--only-batch", dest="only_batch", action="store_true", help="time the batched form only")
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
     ap.add_argument("--single", action="store_true",
                     help="time one form on one n^3 shape (forward only), for profiling")
@@ -490,6 +568,14 @@ def main():
         return
     if args.single:
         run_single(args, local_rank)
+        return
+    if args.only_batch:
+        import torch
+        from paper_1501_07350_gb300 import _build
+        from paper_1501_07350_gb300 import openfft as of
+        _build.build()
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"batch64": measure_batch(of, torch, torch.cuda.current_stream())}))
         return
     if world > 1:
         import torch

@@ -208,6 +208,35 @@ int openfft_get_timing(openfft_plan_t plan, double ms[4], int64_t launches[4]);
 int openfft_redistribute(openfft_plan_t plan, int exchange, int variant,
                          const void* in, void* out);
 
+/* ------------------------------------------------------------ batched -- */
+
+/* Plan `count` independent 3-D transforms of uneven sizes, run together in one
+ * persistent kernel launch replayed from a captured CUDA graph.  NaNbNc: host
+ * array of 3*count sizes (transform i is [NaNbNc[3i]][NaNbNc[3i+1]][NaNbNc[3i+2]]);
+ * P: host array of count rank counts (each transform uses the decomposition of
+ * Eqs. 2-9 with its own P).  dtype: OPENFFT_C2C_F32 (complex64, FP32) or
+ * OPENFFT_C2C_F64 (complex128, double-float).  The plan allocates each
+ * transform's scratch array, the twiddle tables and the work-queue tables.
+ * Returns NULL on error. */
+openfft_plan_t openfft_plan_many(int count, const int* NaNbNc, const int* P, int dtype);
+
+/* Execute all transforms of a batched plan.  in / out: host arrays of `count`
+ * DEVICE pointers (transform i reads in[i], writes out[i], layouts as for
+ * openfft_exec_c2c; in[i] != out[i]).  One graph replay runs every stage of
+ * every transform: work items (tiles of lines of one stage of one transform)
+ * are taken from a device queue in stage-major order; an item of stage s
+ * waits (bounded, about one second) for the stage s-1 tiles of its transform.
+ * Ordered after prior work on the plan's stream; the plan's stream waits for
+ * it.  A wait that runs out is reported as OPENFFT_ERR_TIMEOUT by
+ * openfft_sync.  Changing the pointer set waits for earlier replays. */
+int openfft_exec_many(openfft_plan_t plan, const void* const* in, void* const* out, int dir);
+
+/* Test controls of a batched plan: what = 1 sets the wait budget to `value`
+ * clock cycles; what = 2 with value != 0 makes the second-stage items of
+ * transform 0 (forward) wait for one first-stage tile more than exists, so
+ * that their wait runs out (value = 0 undoes it). */
+int openfft_batch_debug(openfft_plan_t plan, int what, long long value);
+
 /* ------------------------------------------------- allocation-free ----- */
 
 /* The same transform as openfft_exec_c2c (fused variant, default arithmetic

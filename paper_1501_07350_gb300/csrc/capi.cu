@@ -18,6 +18,7 @@
 #include "decomp.h"
 #include "fft_stage.h"
 #include "redistribute.h"
+#include "batch.h"
 
 using namespace ofg;
 
@@ -110,6 +111,7 @@ struct openfft_plan_s {
     size_t ev_used = 0;
     double t_ms[4] = {0, 0, 0, 0};
     int64_t t_launch[4] = {0, 0, 0, 0};
+    BatchPlan* batch = nullptr;   // set for plans made by openfft_plan_many
 };
 
 namespace {
@@ -346,6 +348,7 @@ void free_plan(openfft_plan_s* p)
     for (auto& T : p->tt) { cudaFree(T.d_sbase); cudaFree(T.d_rbase); cudaFree(T.d_chunks); }
     cudaFree(p->stage_in); cudaFree(p->stage_out);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+    if (p->batch) batch_destroy(p->batch);
     delete p;
 }
 
@@ -371,6 +374,10 @@ namespace ofg {
 // error reporting for entry points defined in other translation units
 int set_last_error(int status, const char* msg) { return fail(status, msg); }
 }  // namespace ofg
+
+namespace {
+int fail_cstr(int status, const char* msg) { return fail(status, msg); }
+}  // namespace
 
 // =================================================================== ABI ==
 
@@ -516,6 +523,7 @@ int openfft_set_stream(openfft_plan_t plan, void* stream)
 int openfft_exec_c2c(openfft_plan_t plan, const void* in, void* out, int dir)
 {
     if (!plan || !in || !out) return fail(OPENFFT_ERR_INVALID_ARG, "null plan or buffer");
+    if (plan->batch) return fail(OPENFFT_ERR_INVALID_ARG, "batched plan: use openfft_exec_many");
     if (in == out) return fail(OPENFFT_ERR_ALIAS, "in and out must differ (out-of-place only)");
     if (dir != OPENFFT_FORWARD && dir != OPENFFT_BACKWARD) return fail(OPENFFT_ERR_INVALID_ARG, "dir must be -1 or +1");
     const Candidate& c = plan->cands[(size_t)plan->current];
@@ -544,6 +552,11 @@ int openfft_exec_c2c_host(openfft_plan_t plan, const void* host_in, void* host_o
 int openfft_sync(openfft_plan_t plan)
 {
     if (!plan) return fail(OPENFFT_ERR_INVALID_ARG, "null plan");
+    if (plan->batch) {
+        cudaError_t e = cudaStreamSynchronize(plan->stream);
+        if (e) return cuda_fail(e, "stream synchronize");
+        return batch_status(plan->batch, &fail_cstr);
+    }
     cudaError_t e = cudaStreamSynchronize(plan->stream);
     if (e) return cuda_fail(e, "stream synchronize");
     return OPENFFT_OK;
@@ -627,6 +640,40 @@ int openfft_set_tuning(openfft_plan_t plan, int mode, int candidate)
     default:
         return fail(OPENFFT_ERR_INVALID_ARG, "unknown tuning mode");
     }
+}
+
+openfft_plan_t openfft_plan_many(int count, const int* NaNbNc, const int* P, int dtype)
+{
+    int dev = 0, sms = 148;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e) { cuda_fail(e, "cudaGetDevice"); return nullptr; }
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if ((e = stage_kernels_init(200 * 1024))) { cuda_fail(e, "kernel attributes"); return nullptr; }
+    BatchPlan* b = nullptr;
+    if (batch_create(count, NaNbNc, P, dtype, sms, &b, &fail_cstr)) return nullptr;
+    openfft_plan_s* p = new openfft_plan_s();
+    p->Na = NaNbNc[0]; p->Nb = NaNbNc[1]; p->Nc = NaNbNc[2]; p->P = P[0]; p->dtype = dtype;
+    p->N = 0;
+    p->device = dev; p->sms = sms;
+    p->batch = b;
+    return p;
+}
+
+int openfft_exec_many(openfft_plan_t plan, const void* const* in, void* const* out, int dir)
+{
+    if (!plan || !plan->batch) return fail(OPENFFT_ERR_INVALID_ARG, "not a batched plan (openfft_plan_many)");
+    return batch_exec(plan->batch, in, out, dir, plan->stream, &fail_cstr);
+}
+
+int openfft_batch_debug(openfft_plan_t plan, int what, long long value)
+{
+    if (!plan || !plan->batch) return fail(OPENFFT_ERR_INVALID_ARG, "not a batched plan");
+    if (what == 1) return batch_set_wait_budget(plan->batch, value);
+    if (what == 2) {
+        if (batch_inject_stall(plan->batch, value != 0)) return fail(OPENFFT_ERR_CUDA, "stall injection");
+        return OPENFFT_OK;
+    }
+    return fail(OPENFFT_ERR_INVALID_ARG, "what must be 1 (wait budget) or 2 (stall injection)");
 }
 
 int openfft_set_timing(openfft_plan_t plan, int enable)

@@ -35,6 +35,7 @@ EXPORTS = [
     "openfft_decomp_box", "openfft_decomp_counts", "openfft_decomp_degree", "openfft_set_tuning",
     "openfft_num_candidates", "openfft_candidate", "openfft_current_candidate", "openfft_redistribute",
     "openfft_set_timing", "openfft_get_timing", "openfft_exec_c2c_noalloc",
+    "openfft_plan_many", "openfft_exec_many", "openfft_batch_debug",
 ]
 
 _lock = threading.Lock()
@@ -87,6 +88,9 @@ def load():
             "openfft_set_timing": (i32, [vp, i32]),
             "openfft_get_timing": (i32, [vp, ctypes.POINTER(ctypes.c_double), p64]),
             "openfft_exec_c2c_noalloc": (i32, [i32, i32, i32, i32, i32, vp, vp, i32, vp]),
+            "openfft_plan_many": (vp, [i32, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), i32]),
+            "openfft_exec_many": (i32, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32]),
+            "openfft_batch_debug": (i32, [vp, i32, ctypes.c_longlong]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -217,6 +221,28 @@ def openfft_exec_c2c_noalloc(Na: int, Nb: int, Nc: int, P: int, dtype: int, inp,
     """Plan-free transform that allocates nothing (static device scratch, 16 MiB)."""
     raw = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     _check(load().openfft_exec_c2c_noalloc(Na, Nb, Nc, P, dtype, _ptr(inp), _ptr(out), direction, raw))
+
+
+def openfft_plan_many(shapes, Ps, dtype: int) -> int:
+    """Batched plan of len(shapes) transforms; shapes: [(Na, Nb, Nc)], Ps: [P]."""
+    count = len(shapes)
+    dims = (ctypes.c_int * (3 * count))(*[int(v) for sh in shapes for v in sh])
+    ps = (ctypes.c_int * count)(*[int(p) for p in Ps])
+    h = load().openfft_plan_many(count, dims, ps, dtype)
+    if not h:
+        raise OpenFFTError(load().openfft_last_status(), last_error())
+    return h
+
+
+def openfft_exec_many(plan: int, inputs, outputs, direction: int) -> None:
+    count = len(inputs)
+    ins = (ctypes.c_void_p * count)(*[_ptr(x) for x in inputs])
+    outs = (ctypes.c_void_p * count)(*[_ptr(x) for x in outputs])
+    _check(load().openfft_exec_many(plan, ins, outs, direction))
+
+
+def openfft_batch_debug(plan: int, what: int, value: int) -> None:
+    _check(load().openfft_batch_debug(plan, what, value))
 
 
 # ------------------------------------------------------- convenience ----
