@@ -101,7 +101,7 @@ enum { OPENFFT_ARITH_NATIVE = 0, OPENFFT_ARITH_DOUBLE_FLOAT = 1 };
 enum {
     OPENFFT_TUNE_DEFAULT = 0,    /* fixed default variant                         */
     OPENFFT_TUNE_EXHAUSTIVE = 1, /* time every candidate twice, keep the fastest   */
-    OPENFFT_TUNE_LEARNED = 2,    /* cost-model proposal (falls back to DEFAULT)    */
+    OPENFFT_TUNE_LEARNED = 2,    /* the installed cost model's fastest candidate (no model: DEFAULT) */
     OPENFFT_TUNE_USER = 3        /* candidate index given by the caller            */
 };
 
@@ -201,6 +201,49 @@ int openfft_current_candidate(openfft_plan_t plan);
  * waits for the stream). */
 int openfft_set_timing(openfft_plan_t plan, int enable);
 int openfft_get_timing(openfft_plan_t plan, double ms[4], int64_t launches[4]);
+
+/* ------------------------------------------------ learned cost model -- */
+
+/* The run-time choice of Sec. 3.2.3 made by a learned cost model instead of
+ * timing every candidate: a multilayer perceptron (d inputs -> H tanh -> H
+ * tanh -> 1) predicts the natural logarithm of a candidate's execution time
+ * in milliseconds from features of the problem (sizes, P, dtype) and of the
+ * candidate (the training in learned.py subtracts each problem's mean log
+ * time: only the order of one problem's candidates matters to the pick).
+ * It is trained on the timings the exhaustive tuner measures
+ * (openfft_tune_times), on the GPU, by this library's kernels.
+ *
+ * Parameters are a flat float array of openfft_mlp_num_params(d, H) values:
+ * W1[d][H], b1[H], W2[H][H], b2[H], W3[H], b3 (row-major; layer k computes
+ * act(x W_k + b_k)).  X: n rows of d features (row-major), y: n targets.  All
+ * arrays are HOST arrays; the functions copy to and from the device and
+ * return when done. */
+int openfft_mlp_num_params(int d, int hidden);
+/* yhat[s] = f(X[s]). */
+int openfft_mlp_predict(int d, int hidden, const float* params, const float* X, int n, float* yhat);
+/* Mean squared error over the n samples and its gradient w.r.t. params. */
+int openfft_mlp_loss_grad(int d, int hidden, const float* params, const float* X, const float* y, int n,
+                          float* loss, float* grad);
+/* `steps` full-batch Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, learning
+ * rate lr) from the given params, updated in place; losses (may be NULL)
+ * receives the loss before each step.  One step is captured in a CUDA graph
+ * and replayed. */
+int openfft_mlp_train(int d, int hidden, const float* X, const float* y, int n, int steps, float lr,
+                      float* params, float* losses);
+
+/* Number of features per (problem, candidate) (the model's d). */
+int openfft_num_features(void);
+/* Features of candidate `index` of `plan` (openfft_num_features() floats). */
+int openfft_candidate_features(openfft_plan_t plan, int index, float* features);
+/* Time every candidate of `plan` twice (the faster run is kept) on
+ * plan-owned buffers; ms[i] = -1 for a candidate that cannot run.  This is the
+ * dataset writer of the learned model and the judge of its regret.  The
+ * current selection is kept. */
+int openfft_tune_times(openfft_plan_t plan, float* ms);
+/* Install (params != NULL) or remove the process-wide cost model used by
+ * OPENFFT_TUNE_LEARNED; d must equal openfft_num_features().  The
+ * parameters are copied. */
+int openfft_set_cost_model(int d, int hidden, const float* params);
 
 /* One transpose alone (for testing the permutation): `in` holds the source
  * ordering, `out` receives the destination ordering, bit for bit.

@@ -11,6 +11,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -377,6 +379,73 @@ int set_last_error(int status, const char* msg) { return fail(status, msg); }
 
 namespace {
 int fail_cstr(int status, const char* msg) { return fail(status, msg); }
+
+// ---------------------------------------------------------- cost model --
+
+constexpr int kFeatures = 17;
+
+// Features of (problem, candidate) for the learned cost model.
+void candidate_features(const openfft_plan_s* p, const Candidate& c, float* f)
+{
+    auto l2 = [](double x) { return (float)std::log2(x); };
+    auto pow2 = [](int n) { return (n & (n - 1)) == 0 ? 1.f : 0.f; };
+    f[0] = l2(p->Na) / 10.f; f[1] = l2(p->Nb) / 10.f; f[2] = l2(p->Nc) / 10.f;
+    f[3] = l2((double)p->N) / 30.f;
+    f[4] = l2(p->P) / 10.f;
+    f[5] = p->dtype == OPENFFT_C2C_F64 ? 1.f : 0.f;
+    f[6] = 0.f;                                            // log2(batch) / 7, batch = 1
+    f[7] = c.variant == OPENFFT_VARIANT_FUSED ? 1.f : 0.f;
+    f[8] = c.variant == OPENFFT_VARIANT_PACK_UNPACK ? 1.f : 0.f;
+    f[9] = c.variant == OPENFFT_VARIANT_PACK_EXCHANGE_UNPACK ? 1.f : 0.f;
+    f[10] = c.arith == ARITH_DF ? 1.f : 0.f;
+    f[11] = c.arith == ARITH_F64 ? 1.f : 0.f;
+    f[12] = l2(c.G) / 4.f;
+    f[13] = (c.family == KERNEL_AUTO || c.family == KERNEL_WARP) ? 1.f : 0.f;
+    f[14] = c.family == KERNEL_TILE ? 1.f : 0.f;
+    f[15] = c.family == KERNEL_GENERIC ? 1.f : 0.f;
+    f[16] = (pow2(p->Na) + pow2(p->Nb) + pow2(p->Nc)) / 3.f;
+}
+
+std::mutex g_model_mu;
+std::vector<float> g_model;          // parameters of the installed cost model
+int g_model_d = 0, g_model_h = 0;
+
+// Time every candidate twice (the paper's two runs per method) on plan-owned
+// buffers and keep the faster run; the current selection is restored.
+int time_candidates(openfft_plan_s* p, std::vector<float>& ms)
+{
+    const size_t bytes = (size_t)p->N * (p->dtype == OPENFFT_C2C_F32 ? 8 : 16);
+    void *tin = nullptr, *tout = nullptr;
+    if (cudaMalloc(&tin, bytes) || cudaMalloc(&tout, bytes)) {
+        cudaGetLastError(); cudaFree(tin);
+        return fail(OPENFFT_ERR_NOMEM, "tuning buffers");
+    }
+    cudaMemsetAsync(tin, 0, bytes, p->stream);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0); cudaEventCreate(&e1);
+    const int keep = p->current;
+    int st = OPENFFT_OK;
+    ms.assign(p->cands.size(), -1.f);
+    for (int i = 0; i < (int)p->cands.size() && !st; ++i) {
+        if (select_candidate(p, i)) { g_status = OPENFFT_OK; continue; }   // not buildable here
+        float best = 1e30f;
+        for (int rep = 0; rep < 2 && !st; ++rep) {
+            cudaEventRecord(e0, p->stream);
+            st = openfft_exec_c2c(p, tin, tout, OPENFFT_FORWARD);
+            cudaEventRecord(e1, p->stream);
+            cudaEventSynchronize(e1);
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            best = t < best ? t : best;
+        }
+        ms[(size_t)i] = best;
+    }
+    cudaEventDestroy(e0); cudaEventDestroy(e1);
+    cudaFree(tin); cudaFree(tout);
+    select_candidate(p, keep);
+    return st;
+}
+
 }  // namespace
 
 // =================================================================== ABI ==
@@ -599,47 +668,75 @@ int openfft_current_candidate(openfft_plan_t plan) { return plan ? plan->current
 int openfft_set_tuning(openfft_plan_t plan, int mode, int candidate)
 {
     if (!plan) return fail(OPENFFT_ERR_INVALID_ARG, "null plan");
+    if (plan->batch) return fail(OPENFFT_ERR_INVALID_ARG, "batched plans have a single execution path");
     switch (mode) {
     case OPENFFT_TUNE_DEFAULT:
-    case OPENFFT_TUNE_LEARNED:
         return select_candidate(plan, 0);
     case OPENFFT_TUNE_USER:
         return select_candidate(plan, candidate);
     case OPENFFT_TUNE_EXHAUSTIVE: {
-        const size_t bytes = (size_t)plan->N * (plan->dtype == OPENFFT_C2C_F32 ? 8 : 16);
-        void *tin = nullptr, *tout = nullptr;
-        if (cudaMalloc(&tin, bytes) || cudaMalloc(&tout, bytes)) {
-            cudaGetLastError(); cudaFree(tin);
-            return fail(OPENFFT_ERR_NOMEM, "tuning buffers");
-        }
-        cudaMemsetAsync(tin, 0, bytes, plan->stream);
-        cudaEvent_t e0, e1;
-        cudaEventCreate(&e0); cudaEventCreate(&e1);
-        int best = -1; float best_ms = 0.f;
-        int st = OPENFFT_OK;
-        for (int i = 0; i < (int)plan->cands.size() && !st; ++i) {
-            if (select_candidate(plan, i)) { st = OPENFFT_OK; g_status = OPENFFT_OK; continue; }
-            float ms_min = 1e30f;
-            for (int rep = 0; rep < 2 && !st; ++rep) {        // Sec. 3.2.3: each method twice
-                cudaEventRecord(e0, plan->stream);
-                st = openfft_exec_c2c(plan, tin, tout, OPENFFT_FORWARD);
-                cudaEventRecord(e1, plan->stream);
-                cudaEventSynchronize(e1);
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                ms_min = ms < ms_min ? ms : ms_min;
-            }
-            if (!st && (best < 0 || ms_min < best_ms)) { best = i; best_ms = ms_min; }
-        }
-        cudaEventDestroy(e0); cudaEventDestroy(e1);
-        cudaFree(tin); cudaFree(tout);
+        std::vector<float> ms;
+        int st = time_candidates(plan, ms);
         if (st) return st;
+        int best = -1;
+        for (int i = 0; i < (int)ms.size(); ++i)
+            if (ms[(size_t)i] >= 0.f && (best < 0 || ms[(size_t)i] < ms[(size_t)best])) best = i;
         if (best < 0) return fail(OPENFFT_ERR_UNSUPPORTED, "no candidate ran");
         return select_candidate(plan, best);
+    }
+    case OPENFFT_TUNE_LEARNED: {
+        std::vector<float> model;
+        int d, h;
+        {
+            std::lock_guard<std::mutex> lk(g_model_mu);
+            model = g_model; d = g_model_d; h = g_model_h;
+        }
+        if (model.empty()) return select_candidate(plan, 0);          // no model: the default
+        const int nc = (int)plan->cands.size();
+        std::vector<float> X((size_t)nc * kFeatures), y((size_t)nc);
+        for (int i = 0; i < nc; ++i) candidate_features(plan, plan->cands[(size_t)i], &X[(size_t)i * kFeatures]);
+        int st = openfft_mlp_predict(d, h, model.data(), X.data(), nc, y.data());
+        if (st) return st;
+        // lowest predicted time; a candidate that cannot be built falls back to the next
+        std::vector<int> order((size_t)nc);
+        for (int i = 0; i < nc; ++i) order[(size_t)i] = i;
+        std::sort(order.begin(), order.end(), [&](int a2, int b2) { return y[(size_t)a2] < y[(size_t)b2]; });
+        for (int i : order) if (!select_candidate(plan, i)) return OPENFFT_OK;
+        return fail(OPENFFT_ERR_UNSUPPORTED, "no candidate can be built");
     }
     default:
         return fail(OPENFFT_ERR_INVALID_ARG, "unknown tuning mode");
     }
+}
+
+int openfft_num_features(void) { return kFeatures; }
+
+int openfft_candidate_features(openfft_plan_t plan, int index, float* features)
+{
+    if (!plan || plan->batch || !features || index < 0 || index >= (int)plan->cands.size())
+        return fail(OPENFFT_ERR_INVALID_ARG, "bad plan, candidate or output");
+    candidate_features(plan, plan->cands[(size_t)index], features);
+    return OPENFFT_OK;
+}
+
+int openfft_tune_times(openfft_plan_t plan, float* ms)
+{
+    if (!plan || plan->batch || !ms) return fail(OPENFFT_ERR_INVALID_ARG, "bad plan or output");
+    std::vector<float> t;
+    int st = time_candidates(plan, t);
+    if (st) return st;
+    std::memcpy(ms, t.data(), t.size() * sizeof(float));
+    return OPENFFT_OK;
+}
+
+int openfft_set_cost_model(int d, int hidden, const float* params)
+{
+    std::lock_guard<std::mutex> lk(g_model_mu);
+    if (!params) { g_model.clear(); g_model_d = g_model_h = 0; return OPENFFT_OK; }
+    if (d != kFeatures || hidden < 1 || hidden > 256) return fail(OPENFFT_ERR_INVALID_ARG, "model input size must equal openfft_num_features()");
+    g_model.assign(params, params + openfft_mlp_num_params(d, hidden));
+    g_model_d = d; g_model_h = hidden;
+    return OPENFFT_OK;
 }
 
 openfft_plan_t openfft_plan_many(int count, const int* NaNbNc, const int* P, int dtype)

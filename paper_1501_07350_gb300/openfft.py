@@ -36,6 +36,8 @@ EXPORTS = [
     "openfft_num_candidates", "openfft_candidate", "openfft_current_candidate", "openfft_redistribute",
     "openfft_set_timing", "openfft_get_timing", "openfft_exec_c2c_noalloc",
     "openfft_plan_many", "openfft_exec_many", "openfft_batch_debug",
+    "openfft_mlp_num_params", "openfft_mlp_predict", "openfft_mlp_loss_grad", "openfft_mlp_train",
+    "openfft_num_features", "openfft_candidate_features", "openfft_tune_times", "openfft_set_cost_model",
 ]
 
 _lock = threading.Lock()
@@ -66,6 +68,7 @@ def load():
         i32, i64, vp = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
         p64 = ctypes.POINTER(ctypes.c_int64)
         pi32 = ctypes.POINTER(ctypes.c_int)
+        pf = ctypes.POINTER(ctypes.c_float)
         sig = {
             "openfft_plan": (vp, [i32, i32, i32, i32, i32]),
             "openfft_exec_c2c": (i32, [vp, vp, vp, i32]),
@@ -91,6 +94,14 @@ def load():
             "openfft_plan_many": (vp, [i32, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), i32]),
             "openfft_exec_many": (i32, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32]),
             "openfft_batch_debug": (i32, [vp, i32, ctypes.c_longlong]),
+            "openfft_mlp_num_params": (i32, [i32, i32]),
+            "openfft_mlp_predict": (i32, [i32, i32, pf, pf, i32, pf]),
+            "openfft_mlp_loss_grad": (i32, [i32, i32, pf, pf, pf, i32, pf, pf]),
+            "openfft_mlp_train": (i32, [i32, i32, pf, pf, i32, i32, ctypes.c_float, pf, pf]),
+            "openfft_num_features": (i32, []),
+            "openfft_candidate_features": (i32, [vp, i32, pf]),
+            "openfft_tune_times": (i32, [vp, pf]),
+            "openfft_set_cost_model": (i32, [i32, i32, pf]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -243,6 +254,67 @@ def openfft_exec_many(plan: int, inputs, outputs, direction: int) -> None:
 
 def openfft_batch_debug(plan: int, what: int, value: int) -> None:
     _check(load().openfft_batch_debug(plan, what, value))
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _pf(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def openfft_mlp_num_params(d: int, hidden: int) -> int:
+    return int(load().openfft_mlp_num_params(d, hidden))
+
+
+def openfft_mlp_predict(d: int, hidden: int, params, X) -> np.ndarray:
+    params, X = _f32(params), _f32(X)
+    n = X.shape[0]
+    yhat = np.empty(n, dtype=np.float32)
+    _check(load().openfft_mlp_predict(d, hidden, _pf(params), _pf(X), n, _pf(yhat)))
+    return yhat
+
+
+def openfft_mlp_loss_grad(d: int, hidden: int, params, X, y):
+    params, X, y = _f32(params), _f32(X), _f32(y)
+    loss = np.zeros(1, dtype=np.float32)
+    grad = np.empty_like(params)
+    _check(load().openfft_mlp_loss_grad(d, hidden, _pf(params), _pf(X), _pf(y), X.shape[0], _pf(loss), _pf(grad)))
+    return float(loss[0]), grad
+
+
+def openfft_mlp_train(d: int, hidden: int, X, y, steps: int, lr: float, params):
+    """Returns (trained params, loss before each step)."""
+    X, y = _f32(X), _f32(y)
+    p = _f32(params).copy()
+    losses = np.empty(steps, dtype=np.float32)
+    _check(load().openfft_mlp_train(d, hidden, _pf(X), _pf(y), X.shape[0], steps, lr, _pf(p), _pf(losses)))
+    return p, losses
+
+
+def openfft_num_features() -> int:
+    return int(load().openfft_num_features())
+
+
+def openfft_candidate_features(plan: int, index: int) -> np.ndarray:
+    f = np.empty(openfft_num_features(), dtype=np.float32)
+    _check(load().openfft_candidate_features(plan, index, _pf(f)))
+    return f
+
+
+def openfft_tune_times(plan: int) -> np.ndarray:
+    ms = np.empty(openfft_num_candidates(plan), dtype=np.float32)
+    _check(load().openfft_tune_times(plan, _pf(ms)))
+    return ms
+
+
+def openfft_set_cost_model(d: int, hidden: int, params) -> None:
+    if params is None:
+        _check(load().openfft_set_cost_model(d, hidden, None))
+    else:
+        p = _f32(params)
+        _check(load().openfft_set_cost_model(d, hidden, _pf(p)))
 
 
 # ------------------------------------------------------- convenience ----

@@ -134,3 +134,21 @@ def test_null_plan_is_rejected():
     assert lib.openfft_exec_c2c(None, None, None, -1) == of.ERR_INVALID_ARG
     assert lib.openfft_set_tuning(None, 0, 0) == of.ERR_INVALID_ARG
     lib.openfft_destroy(None)      # NULL-safe
+
+
+def test_committed_learned_data_is_consistent():
+    """The committed timing dataset covers the held-out benchmark problems and the
+    committed cost model has the library's feature count."""
+    import json
+    from paper_1501_07350_gb300 import learned
+    rows = learned.load_rows()
+    train_rows, test_rows = learned.split(rows)
+    assert len(test_rows) == len(learned.HELD_OUT) and len(train_rows) > 50
+    for r in rows:
+        assert len(r["ms"]) == len(r["features"]) == len(r["candidates"])
+        assert all(len(f) == of.openfft_num_features() for f in r["features"])
+    with open(learned.MODEL_FILE) as fh:
+        model = json.load(fh)
+    assert model["d"] == of.openfft_num_features()
+    assert len(model["params"]) == of.openfft_mlp_num_params(model["d"], model["hidden"])
+    assert model["held_out"]["mean_regret"] <= 0.05
