@@ -58,22 +58,34 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+STAGE_SOURCES = ("fft_warp.cuh", "fft_tile.cuh", "stage_io.cuh", "arith.cuh", "fft_stage.h", "generic_stage.cuh",
+                 "fft_stage.cu", "fft_tile_df.cu")
+
+
 def stage_source_hash() -> str:
+    """Hash of the stage-kernel sources: a committed DRAM-traffic figure is only
+    reported while the kernel it was measured on is unchanged."""
     h = hashlib.sha256()
-    for f in ("fft_stage.cu", "arith.cuh", "fft_stage.h"):
+    for f in STAGE_SOURCES:
         with open(os.path.join(ROOT, "paper_1501_07350_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def profiled_traffic(kernel_hash: str):
-    """DRAM bytes per stage launch from a committed ncu summary, if it was taken on this source."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per stage launch from the committed ncu summary of the dominant
+    kernel, if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "fft_warp_kernel_df_256cubed.md")
+    vals = {}
     try:
         with open(path) as fh:
-            d = json.load(fh)
-        if d.get("source_hash") == kernel_hash:
-            return float(d["dram_bytes_per_launch"])
+            for line in fh:
+                line = line.strip()
+                for key in ("source_hash:", "dram_bytes_per_launch:"):
+                    if line.startswith(key):
+                        vals[key[:-1]] = line[len(key):].strip()
+        if vals.get("source_hash") == kernel_hash:
+            return float(vals["dram_bytes_per_launch"])
     except Exception:
         pass
     return None
@@ -130,6 +142,24 @@ class ClockSampler:
         pw = [num(r[4]) for r in rows if num(r[4]) is not None]
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+# ------------------------------------------------------- multi-rank ----
+
+def reduce_max(value: float, world: int, device) -> float:
+    """Maximum of `value` over all ranks (the slowest rank sets the step time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(work_per_rank_step: float, world: int, ms_per_step: float) -> float:
+    """Whole-job throughput (GFLOP/s): every rank's work over the slowest rank's time."""
+    return world * work_per_rank_step / (ms_per_step * 1e-3) / 1e9
 
 
 # ------------------------------------------------------------------ ours --
@@ -209,14 +239,10 @@ def run_ours(args, rank, world, local_rank):
     for k in ("fft", "buffer_comm", "communication"):
         launches += phases[k]["launches"]
 
-    t_max = ms_total
-    if world > 1:
-        tt = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = reduce_max(ms_total, world, dev)
     ms_per_step = t_max / args.steps
     work_per_step = 2 * len(PS) * flops(N)
-    value = world * work_per_step / (ms_per_step * 1e-3) / 1e9
+    value = job_value(work_per_step, world, ms_per_step)
 
     # correctness of the timed outputs (round trip) on this rank
     rt_err = float(torch.linalg.vector_norm(z - x) / torch.linalg.vector_norm(x))
@@ -252,12 +278,8 @@ def run_ours(args, rank, world, local_rank):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         host_step()
-    t_e2e = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
-    e2e = {"value": round(world * work_per_step / t_e2e / 1e9, 2), "unit": UNIT,
+    t_e2e = reduce_max((time.perf_counter() - t0) / e2e_steps, world, dev)
+    e2e = {"value": round(job_value(work_per_step, world, t_e2e * 1e3), 2), "unit": UNIT,
            "h2d_bytes_per_step": 2 * len(PS) * N * 16, "d2h_bytes_per_step": 2 * len(PS) * N * 16,
            "steps": e2e_steps}
 
