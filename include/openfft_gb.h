@@ -69,23 +69,34 @@ enum {
     OPENFFT_ERR_UNSUPPORTED = 8        /* the request is valid but this build does not do it */
 };
 
-/* Transpose variants (the paper's communication methods, Sec. 3.2.1, recast
- * for ranks that share one memory).
- *   FUSED (V2):       the transpose is folded into the store of each FFT stage:
- *                     one HBM read and one write per stage.
- *   PACK_EXCHANGE_UNPACK (V0): the stage stores its box unchanged, then a pack
- *                     kernel builds per-destination send segments (ascending
- *                     source index), an exchange kernel moves every segment to
- *                     its receiver as one all-to-all with variable counts
- *                     (Isend/Irecv + Waitall, Alltoallv), and an unpack kernel
- *                     writes the next ordering.
- *   PACK_UNPACK (V1): as V0 but each receiver unpacks straight from the
- *                     senders' segments (the unpack-on-arrival of Isend_Waitsome).
- */
+/* Transpose variants: the paper's six communication methods (Sec. 3.2.1),
+ * recast for ranks that share one memory, and the fused form.
+ *   FUSED (V2):  the transpose is folded into the store of each FFT stage: one
+ *                HBM read and one write per stage (the default).
+ * The explicit methods store each stage's box unchanged, pack per-destination
+ * send segments (ascending source index, step (4) of Sec. 3.1.1), move them
+ * (step (5)) and unpack them into the next ordering (step (6)):
+ *   PACK_EXCHANGE_UNPACK (Alltoallv): one exchange over the count matrix, then
+ *                unpack;
+ *   ISEND_WAITALL:       every sender's segments moved in its own launch (P
+ *                launches), then unpack;
+ *   ISEND_WAITALL_BLOCK: ranks in groups of B_SIZE = 32; ceil(P/32) steps, step
+ *                k moving the pairs (r, s) with floor(s/32) = (floor(r/32) + k)
+ *                mod ceil(P/32); then unpack;
+ *   PACK_UNPACK (Isend_Waitsome): every receiver unpacks straight from the
+ *                senders' segments (unpack on arrival);
+ *   ISEND_WAITSOME_BLOCK: the blocked steps, each unpacking its segments on
+ *                arrival;
+ *   SENDRECV:    P shifted steps, step i moving the pairs (r, (r + i) mod P),
+ *                then unpack. */
 enum {
     OPENFFT_VARIANT_PACK_EXCHANGE_UNPACK = 0,
     OPENFFT_VARIANT_PACK_UNPACK = 1,
-    OPENFFT_VARIANT_FUSED = 2
+    OPENFFT_VARIANT_FUSED = 2,
+    OPENFFT_VARIANT_ISEND_WAITALL = 3,
+    OPENFFT_VARIANT_ISEND_WAITALL_BLOCK = 4,
+    OPENFFT_VARIANT_ISEND_WAITSOME_BLOCK = 5,
+    OPENFFT_VARIANT_SENDRECV = 6
 };
 
 /* Arithmetic used for OPENFFT_C2C_F64.
@@ -208,8 +219,9 @@ int openfft_get_timing(openfft_plan_t plan, double ms[4], int64_t launches[4]);
  * timing every candidate: a multilayer perceptron (d inputs -> H tanh -> H
  * tanh -> 1) predicts the natural logarithm of a candidate's execution time
  * in milliseconds from features of the problem (sizes, P, dtype) and of the
- * candidate (the training in learned.py subtracts each problem's mean log
- * time: only the order of one problem's candidates matters to the pick).
+ * candidate (learned.py trains on the log ratio to the problem's fastest
+ * candidate, capped at 1: only the order of one problem's candidates matters
+ * to the pick).
  * It is trained on the timings the exhaustive tuner measures
  * (openfft_tune_times), on the GPU, by this library's kernels.
  *
@@ -240,10 +252,12 @@ int openfft_candidate_features(openfft_plan_t plan, int index, float* features);
  * dataset writer of the learned model and the judge of its regret.  The
  * current selection is kept. */
 int openfft_tune_times(openfft_plan_t plan, float* ms);
-/* Install (params != NULL) or remove the process-wide cost model used by
- * OPENFFT_TUNE_LEARNED; d must equal openfft_num_features().  The
+/* Install (params != NULL, count >= 1) or remove (params == NULL) the
+ * process-wide cost model used by OPENFFT_TUNE_LEARNED: an ensemble of
+ * `count` networks whose predictions are averaged; params holds count
+ * consecutive parameter sets.  d must equal openfft_num_features().  The
  * parameters are copied. */
-int openfft_set_cost_model(int d, int hidden, const float* params);
+int openfft_set_cost_model(int count, int d, int hidden, const float* params);
 
 /* One transpose alone (for testing the permutation): `in` holds the source
  * ordering, `out` receives the destination ordering, bit for bit.

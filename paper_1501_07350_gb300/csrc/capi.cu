@@ -68,7 +68,7 @@ struct Candidate {
 };
 
 // one step of an execution
-enum OpKind { OP_STAGE, OP_PACK, OP_EXCHANGE, OP_UNPACK };
+enum OpKind { OP_STAGE, OP_PACK, OP_EXCHANGE, OP_UNPACK, OP_SEG_EXCHANGE, OP_SEG_UNPACK };
 enum Buf { B_IN, B_OUT, B_A, B_B };
 
 struct Op {
@@ -77,6 +77,8 @@ struct Op {
     StageLaunch stage;       // OP_STAGE
     int tix;                 // transpose table index (0..3) for pack/exchange/unpack
     int from_send;           // OP_UNPACK
+    int sched;               // OP_SEG_*: SCHED_*
+    int64_t step;            // OP_SEG_*: step of the schedule
 };
 
 struct TransposeTables {
@@ -86,6 +88,9 @@ struct TransposeTables {
     int64_t* d_rbase = nullptr;
     int64_t* d_chunks = nullptr;
     int64_t nchunks = 0;
+    int64_t* d_C = nullptr;       // count matrix [r*P+s]
+    int64_t* d_sdispl = nullptr;  // send displacement of segment (r, s) [r*P+s]
+    int64_t* d_rdispl = nullptr;  // receive displacement of segment (r, s) [s*P+r]
 };
 
 }  // namespace
@@ -167,11 +172,60 @@ Op stage_op(int src, int dst, const StageLaunch& L)
     return o;
 }
 
-Op redist_op(OpKind k, int src, int dst, int tix, int from_send)
+Op redist_op(OpKind k, int src, int dst, int tix, int from_send, int sched = 0, int64_t step = 0)
 {
     Op o; std::memset(&o, 0, sizeof(o));
     o.kind = k; o.src = src; o.dst = dst; o.tix = tix; o.from_send = from_send;
+    o.sched = sched; o.step = step;
     return o;
+}
+
+// The paper's communication methods (Sec. 3.2.1) as the ops of one transpose
+// from buffer `from` (send segments go to `other`): returns where the
+// destination ordering lands (`final_to` if given).
+int transpose_ops(std::vector<Op>& ops, int variant, int tix, int from, int final_to, int64_t P)
+{
+    const int other = from == B_A ? B_B : B_A;
+    ops.push_back(redist_op(OP_PACK, from, other, tix, 0));             // step (4)
+    int landing;
+    auto stepped_exchange = [&](int sched) {                            // step (5), in steps
+        const int64_t n = num_steps(sched, P, kBlockSize);
+        for (int64_t k = 0; k < n; ++k) ops.push_back(redist_op(OP_SEG_EXCHANGE, other, from, tix, 0, sched, k));
+    };
+    switch (variant) {
+    case OPENFFT_VARIANT_PACK_EXCHANGE_UNPACK:                          // Alltoallv
+        ops.push_back(redist_op(OP_EXCHANGE, other, from, tix, 0));
+        landing = final_to >= 0 ? final_to : other;
+        ops.push_back(redist_op(OP_UNPACK, from, landing, tix, 0));
+        break;
+    case OPENFFT_VARIANT_ISEND_WAITALL:
+        stepped_exchange(SCHED_PER_SENDER);
+        landing = final_to >= 0 ? final_to : other;
+        ops.push_back(redist_op(OP_UNPACK, from, landing, tix, 0));
+        break;
+    case OPENFFT_VARIANT_ISEND_WAITALL_BLOCK:
+        stepped_exchange(SCHED_BLOCKED);
+        landing = final_to >= 0 ? final_to : other;
+        ops.push_back(redist_op(OP_UNPACK, from, landing, tix, 0));
+        break;
+    case OPENFFT_VARIANT_SENDRECV:
+        stepped_exchange(SCHED_SHIFTED);
+        landing = final_to >= 0 ? final_to : other;
+        ops.push_back(redist_op(OP_UNPACK, from, landing, tix, 0));
+        break;
+    case OPENFFT_VARIANT_ISEND_WAITSOME_BLOCK: {                         // unpack each group's segments
+        landing = final_to >= 0 ? final_to : from;
+        const int64_t n = num_steps(SCHED_BLOCKED, P, kBlockSize);
+        for (int64_t k = 0; k < n; ++k)
+            ops.push_back(redist_op(OP_SEG_UNPACK, other, landing, tix, 1, SCHED_BLOCKED, k));
+        break;
+    }
+    default:                                                             // Isend_Waitsome
+        landing = final_to >= 0 ? final_to : from;
+        ops.push_back(redist_op(OP_UNPACK, other, landing, tix, 1));
+        break;
+    }
+    return landing;
 }
 
 // Build the forward and backward op lists of candidate c.
@@ -205,24 +259,9 @@ int build_ops(openfft_plan_s* p, const Candidate& c)
         B.push_back(stage_op(B_OUT, B_OUT, L));
         return OPENFFT_OK;
     }
-    // V0 / V1: contiguous stage stores, explicit transposes through A and B
-    const bool v0 = c.variant == OPENFFT_VARIANT_PACK_EXCHANGE_UNPACK;
-    // One transpose starting from buffer `from` (A or B).  Returns the buffer
-    // the destination ordering lands in: `final_to` if given, else a scratch
-    // buffer that is free at that point.
+    // explicit variants: contiguous stage stores, transposes through A and B
     auto transpose = [&](std::vector<Op>& ops, int tix, int from, int final_to) {
-        const int other = from == B_A ? B_B : B_A;
-        ops.push_back(redist_op(OP_PACK, from, other, tix, 0));          // send segments in `other`
-        int landing;
-        if (v0) {
-            ops.push_back(redist_op(OP_EXCHANGE, other, from, tix, 0));  // receive buffers in `from`
-            landing = final_to >= 0 ? final_to : other;
-            ops.push_back(redist_op(OP_UNPACK, from, landing, tix, 0));
-        } else {
-            landing = final_to >= 0 ? final_to : from;
-            ops.push_back(redist_op(OP_UNPACK, other, landing, tix, 1));
-        }
-        return landing;
+        return transpose_ops(ops, c.variant, tix, from, final_to, p->P);
     };
     auto other_of = [](int b) { return b == B_A ? B_B : B_A; };
     // forward
@@ -308,6 +347,12 @@ int run_ops(openfft_plan_s* p, const std::vector<Op>& ops, const void* in, void*
             StageLaunch L = o.stage;
             L.args.in = s; L.args.out = d;
             e = launch_stage(L, p->stream);
+        } else if (o.kind == OP_SEG_EXCHANGE) {
+            const TransposeTables& T = p->tt[o.tix];
+            e = launch_segment_exchange(o.sched, p->P, kBlockSize, o.step, E, T.d_C, T.d_sdispl, T.d_rdispl, s, d, p->stream);
+        } else if (o.kind == OP_SEG_UNPACK) {
+            const TransposeTables& T = p->tt[o.tix];
+            e = launch_segment_unpack(T.t, o.sched, kBlockSize, o.step, E, s, d, T.d_sbase, p->stream);
         } else {
             const TransposeTables& T = p->tt[o.tix];
             if (o.kind == OP_PACK) e = launch_pack(T.t, E, s, d, T.d_sbase, p->N, p->sms, p->stream);
@@ -316,7 +361,7 @@ int run_ops(openfft_plan_s* p, const std::vector<Op>& ops, const void* in, void*
         }
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
         if (p->timing) {
-            const int cat = o.kind == OP_STAGE ? 0 : (o.kind == OP_EXCHANGE ? 2 : 1);
+            const int cat = o.kind == OP_STAGE ? 0 : ((o.kind == OP_EXCHANGE || o.kind == OP_SEG_EXCHANGE) ? 2 : 1);
             int st = record(p, cat);
             if (st) return st;
         }
@@ -347,7 +392,10 @@ void free_plan(openfft_plan_s* p)
     if (!p) return;
     cudaFree(p->bufA); cudaFree(p->bufB);
     for (auto& row : p->tw) for (void* t : row) cudaFree(t);
-    for (auto& T : p->tt) { cudaFree(T.d_sbase); cudaFree(T.d_rbase); cudaFree(T.d_chunks); }
+    for (auto& T : p->tt) {
+        cudaFree(T.d_sbase); cudaFree(T.d_rbase); cudaFree(T.d_chunks);
+        cudaFree(T.d_C); cudaFree(T.d_sdispl); cudaFree(T.d_rdispl);
+    }
     cudaFree(p->stage_in); cudaFree(p->stage_out);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
     if (p->batch) batch_destroy(p->batch);
@@ -382,7 +430,7 @@ int fail_cstr(int status, const char* msg) { return fail(status, msg); }
 
 // ---------------------------------------------------------- cost model --
 
-constexpr int kFeatures = 17;
+constexpr int kFeatures = 21;
 
 // Features of (problem, candidate) for the learned cost model.
 void candidate_features(const openfft_plan_s* p, const Candidate& c, float* f)
@@ -404,11 +452,15 @@ void candidate_features(const openfft_plan_s* p, const Candidate& c, float* f)
     f[14] = c.family == KERNEL_TILE ? 1.f : 0.f;
     f[15] = c.family == KERNEL_GENERIC ? 1.f : 0.f;
     f[16] = (pow2(p->Na) + pow2(p->Nb) + pow2(p->Nc)) / 3.f;
+    f[17] = c.variant == OPENFFT_VARIANT_ISEND_WAITALL ? 1.f : 0.f;
+    f[18] = c.variant == OPENFFT_VARIANT_ISEND_WAITALL_BLOCK ? 1.f : 0.f;
+    f[19] = c.variant == OPENFFT_VARIANT_ISEND_WAITSOME_BLOCK ? 1.f : 0.f;
+    f[20] = c.variant == OPENFFT_VARIANT_SENDRECV ? 1.f : 0.f;
 }
 
 std::mutex g_model_mu;
-std::vector<float> g_model;          // parameters of the installed cost model
-int g_model_d = 0, g_model_h = 0;
+std::vector<float> g_model;          // parameters of the installed cost models (an ensemble)
+int g_model_d = 0, g_model_h = 0, g_model_k = 0;
 
 // Time every candidate twice (the paper's two runs per method) on plan-owned
 // buffers and keep the faster run; the current selection is restored.
@@ -535,12 +587,13 @@ openfft_plan_t openfft_plan(int Na, int Nb, int Nc, int P, int dtype)
     for (int i = 0; i < 4; ++i) {
         TransposeTables& T = p->tt[i];
         T.t = make_transpose(whichs[i], Na, Nb, Nc, P);
-        std::vector<int64_t> sb, rb, ch;
-        build_transpose_tables(T.t, T.C, sb, rb, ch, 8192);
+        std::vector<int64_t> sb, rb, ch, sd, rd;
+        build_transpose_tables(T.t, T.C, sb, rb, ch, 8192, &sd, &rd);
         T.nchunks = (int64_t)ch.size() / 3;
         const size_t pp = sb.size() * sizeof(int64_t);
         if (cudaMalloc(&T.d_sbase, pp) || cudaMalloc(&T.d_rbase, pp) ||
-            cudaMalloc(&T.d_chunks, ch.size() * sizeof(int64_t) + 8)) {
+            cudaMalloc(&T.d_chunks, ch.size() * sizeof(int64_t) + 8) ||
+            cudaMalloc(&T.d_C, pp) || cudaMalloc(&T.d_sdispl, pp) || cudaMalloc(&T.d_rdispl, pp)) {
             cudaGetLastError();
             fail(OPENFFT_ERR_NOMEM, "transpose table allocation failed");
             free_plan(p);
@@ -549,12 +602,15 @@ openfft_plan_t openfft_plan(int Na, int Nb, int Nc, int P, int dtype)
         cudaMemcpy(T.d_sbase, sb.data(), pp, cudaMemcpyHostToDevice);
         cudaMemcpy(T.d_rbase, rb.data(), pp, cudaMemcpyHostToDevice);
         if (!ch.empty()) cudaMemcpy(T.d_chunks, ch.data(), ch.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+        cudaMemcpy(T.d_C, T.C.data(), pp, cudaMemcpyHostToDevice);
+        cudaMemcpy(T.d_sdispl, sd.data(), pp, cudaMemcpyHostToDevice);
+        cudaMemcpy(T.d_rdispl, rd.data(), pp, cudaMemcpyHostToDevice);
     }
     if ((e = cudaDeviceSynchronize())) { cuda_fail(e, "plan setup"); free_plan(p); return nullptr; }
     // candidates (Sec. 3.2.3: the set the tuner chooses from).  The fused
-    // variant is tried with every stage-kernel family and tile width; the
-    // explicit variants V1 and V0 (the paper's pack / communicate / unpack
-    // methods) with the default kernel.  The first candidate is the default.
+    // variant is tried with every stage-kernel family and tile width; the six
+    // explicit pack / communicate / unpack methods of Sec. 3.2.1 with the
+    // default kernel.  The first candidate is the default.
     {
         std::vector<int> ariths;
         if (dtype == OPENFFT_C2C_F32) ariths = {ARITH_F32};
@@ -569,6 +625,10 @@ openfft_plan_t openfft_plan(int Na, int Nb, int Nc, int P, int dtype)
             p->cands.push_back(Candidate{OPENFFT_VARIANT_FUSED, ar, gw, KERNEL_GENERIC});
             p->cands.push_back(Candidate{OPENFFT_VARIANT_PACK_UNPACK, ar, gw, KERNEL_AUTO});
             p->cands.push_back(Candidate{OPENFFT_VARIANT_PACK_EXCHANGE_UNPACK, ar, gw, KERNEL_AUTO});
+            p->cands.push_back(Candidate{OPENFFT_VARIANT_ISEND_WAITALL, ar, gw, KERNEL_AUTO});
+            p->cands.push_back(Candidate{OPENFFT_VARIANT_ISEND_WAITALL_BLOCK, ar, gw, KERNEL_AUTO});
+            p->cands.push_back(Candidate{OPENFFT_VARIANT_ISEND_WAITSOME_BLOCK, ar, gw, KERNEL_AUTO});
+            p->cands.push_back(Candidate{OPENFFT_VARIANT_SENDRECV, ar, gw, KERNEL_AUTO});
         }
     }
     if (select_candidate(p, 0)) { free_plan(p); return nullptr; }
@@ -686,17 +746,21 @@ int openfft_set_tuning(openfft_plan_t plan, int mode, int candidate)
     }
     case OPENFFT_TUNE_LEARNED: {
         std::vector<float> model;
-        int d, h;
+        int d, h, k;
         {
             std::lock_guard<std::mutex> lk(g_model_mu);
-            model = g_model; d = g_model_d; h = g_model_h;
+            model = g_model; d = g_model_d; h = g_model_h; k = g_model_k;
         }
         if (model.empty()) return select_candidate(plan, 0);          // no model: the default
         const int nc = (int)plan->cands.size();
-        std::vector<float> X((size_t)nc * kFeatures), y((size_t)nc);
+        std::vector<float> X((size_t)nc * kFeatures), y((size_t)nc, 0.f), yk((size_t)nc);
         for (int i = 0; i < nc; ++i) candidate_features(plan, plan->cands[(size_t)i], &X[(size_t)i * kFeatures]);
-        int st = openfft_mlp_predict(d, h, model.data(), X.data(), nc, y.data());
-        if (st) return st;
+        const size_t np = (size_t)openfft_mlp_num_params(d, h);
+        for (int m = 0; m < k; ++m) {                                   // mean prediction of the ensemble
+            int st = openfft_mlp_predict(d, h, model.data() + (size_t)m * np, X.data(), nc, yk.data());
+            if (st) return st;
+            for (int i = 0; i < nc; ++i) y[(size_t)i] += yk[(size_t)i] / (float)k;
+        }
         // lowest predicted time; a candidate that cannot be built falls back to the next
         std::vector<int> order((size_t)nc);
         for (int i = 0; i < nc; ++i) order[(size_t)i] = i;
@@ -729,13 +793,14 @@ int openfft_tune_times(openfft_plan_t plan, float* ms)
     return OPENFFT_OK;
 }
 
-int openfft_set_cost_model(int d, int hidden, const float* params)
+int openfft_set_cost_model(int count, int d, int hidden, const float* params)
 {
     std::lock_guard<std::mutex> lk(g_model_mu);
-    if (!params) { g_model.clear(); g_model_d = g_model_h = 0; return OPENFFT_OK; }
-    if (d != kFeatures || hidden < 1 || hidden > 256) return fail(OPENFFT_ERR_INVALID_ARG, "model input size must equal openfft_num_features()");
-    g_model.assign(params, params + openfft_mlp_num_params(d, hidden));
-    g_model_d = d; g_model_h = hidden;
+    if (!params || count == 0) { g_model.clear(); g_model_d = g_model_h = g_model_k = 0; return OPENFFT_OK; }
+    if (count < 1 || d != kFeatures || hidden < 1 || hidden > 256)
+        return fail(OPENFFT_ERR_INVALID_ARG, "count >= 1 and d == openfft_num_features() required");
+    g_model.assign(params, params + (size_t)count * openfft_mlp_num_params(d, hidden));
+    g_model_d = d; g_model_h = hidden; g_model_k = count;
     return OPENFFT_OK;
 }
 
@@ -826,13 +891,21 @@ int openfft_redistribute(openfft_plan_t plan, int exchange, int variant, const v
         if (st) return st;
         L.args.in = in; L.args.out = out;
         e = launch_stage(L, plan->stream);
-    } else if (variant == OPENFFT_VARIANT_PACK_EXCHANGE_UNPACK) {
-        if (!(e = launch_pack(T.t, E, in, plan->bufA, T.d_sbase, plan->N, plan->sms, plan->stream)))
-            if (!(e = launch_exchange(E, T.d_chunks, T.nchunks, plan->bufA, plan->bufB, plan->sms, plan->stream)))
-                e = launch_unpack(T.t, E, plan->bufB, out, T.d_rbase, 0, plan->N, plan->sms, plan->stream);
-    } else if (variant == OPENFFT_VARIANT_PACK_UNPACK) {
-        if (!(e = launch_pack(T.t, E, in, plan->bufA, T.d_sbase, plan->N, plan->sms, plan->stream)))
-            e = launch_unpack(T.t, E, plan->bufA, out, T.d_sbase, 1, plan->N, plan->sms, plan->stream);
+    } else if (variant >= OPENFFT_VARIANT_PACK_EXCHANGE_UNPACK && variant <= OPENFFT_VARIANT_SENDRECV) {
+        // the ops of one transpose: send segments in A, receive buffers in B
+        std::vector<Op> ops;
+        transpose_ops(ops, variant, tix_of(exchange), B_B, B_OUT, plan->P);
+        for (const Op& o : ops) {
+            const void* src = o.src == B_IN ? in : (o.src == B_OUT ? out : (o.src == B_A ? plan->bufA : plan->bufB));
+            void* dst = o.dst == B_OUT ? out : (o.dst == B_A ? plan->bufA : plan->bufB);
+            if (o.kind == OP_PACK) src = in;                 // the source ordering is the caller's input
+            if (o.kind == OP_PACK) e = launch_pack(T.t, E, src, dst, T.d_sbase, plan->N, plan->sms, plan->stream);
+            else if (o.kind == OP_EXCHANGE) e = launch_exchange(E, T.d_chunks, T.nchunks, src, dst, plan->sms, plan->stream);
+            else if (o.kind == OP_UNPACK) e = launch_unpack(T.t, E, src, dst, o.from_send ? T.d_sbase : T.d_rbase, o.from_send, plan->N, plan->sms, plan->stream);
+            else if (o.kind == OP_SEG_EXCHANGE) e = launch_segment_exchange(o.sched, plan->P, kBlockSize, o.step, E, T.d_C, T.d_sdispl, T.d_rdispl, src, dst, plan->stream);
+            else e = launch_segment_unpack(T.t, o.sched, kBlockSize, o.step, E, src, dst, T.d_sbase, plan->stream);
+            if (e) break;
+        }
     } else {
         return fail(OPENFFT_ERR_INVALID_ARG, "unknown variant");
     }

@@ -72,6 +72,108 @@ __global__ void unpack_kernel(const Transpose t, const E* __restrict__ buf, E* _
     }
 }
 
+// ------------------------------------------------- stepped schedules ----
+//
+// The paper's methods differ in how the P x P segments are scheduled:
+//   per sender  (Isend_Waitall):           step r moves the segments (r, s), all s;
+//   blocked     (Isend_Wait*_Block):       groups of B ranks; step k moves the pairs
+//                                          (r, s) with floor(s/B) = (floor(r/B) + k) mod G,
+//                                          G = ceil(P/B) steps in total;
+//   shifted     (Sendrecv):                step i moves the pairs (r, (r + i) mod P).
+// pair_of maps (step, index within the step) to (r, s); -1 if the index is empty.
+
+__device__ __forceinline__ void pair_of(int sched, int64_t P, int64_t B, int64_t step, int64_t idx,
+                                        int64_t* r, int64_t* s)
+{
+    if (sched == SCHED_PER_SENDER) { *r = step; *s = idx; return; }
+    if (sched == SCHED_SHIFTED) { *r = idx; *s = (idx + step) % P; return; }
+    // blocked: idx = r * B + j
+    const int64_t G = (P + B - 1) / B;
+    const int64_t rr = idx / B, j = idx - rr * B;
+    const int64_t ss = ((rr / B + step) % G) * B + j;
+    *r = rr;
+    *s = ss < P ? ss : -1;
+}
+
+int64_t pairs_per_step(int sched, int64_t P, int64_t B)
+{
+    if (sched == SCHED_BLOCKED) return P * B;
+    return P;
+}
+
+int64_t num_steps(int sched, int64_t P, int64_t B)
+{
+    if (sched == SCHED_BLOCKED) return (P + B - 1) / B;
+    return P;
+}
+
+// one CTA per pair of the step: copy segment (r, s) from its send
+// displacement to its receive displacement
+template <class E>
+__global__ void segment_exchange_kernel(int sched, int64_t P, int64_t B, int64_t step,
+                                        const int64_t* __restrict__ C, const int64_t* __restrict__ sdispl,
+                                        const int64_t* __restrict__ rdispl, const E* __restrict__ send,
+                                        E* __restrict__ recv)
+{
+    int64_t r, s;
+    pair_of(sched, P, B, step, blockIdx.x, &r, &s);
+    if (s < 0) return;
+    const int64_t len = C[r * P + s];
+    const E* src = send + sdispl[r * P + s];
+    E* dst = recv + rdispl[s * P + r];
+    for (int64_t j = threadIdx.x; j < len; j += blockDim.x) dst[j] = src[j];
+}
+
+// one CTA per pair of the step: the receiver takes the elements of segment
+// (r, s) straight from the sender's send buffer and writes them to their
+// places in the destination ordering (unpack on arrival).  Threads walk the
+// source rows of rank r; each row holds a contiguous run of elements for s.
+template <class E>
+__global__ void segment_unpack_kernel(const Transpose t, int sched, int64_t B, int64_t step,
+                                      const E* __restrict__ send, E* __restrict__ dst,
+                                      const int64_t* __restrict__ sbase)
+{
+    const int64_t P = t.src.P;
+    int64_t r, s;
+    pair_of(sched, P, B, step, blockIdx.x, &r, &s);
+    if (s < 0) return;
+    const int64_t R0 = row_begin(t.src, r), R1 = row_begin(t.src, r + 1);
+    const int64_t Q0 = row_begin(t.dst, s), Q1 = row_begin(t.dst, s + 1);
+    const int64_t base = sbase[r * P + s];
+    for (int64_t q = R0 + threadIdx.x; q < R1; q += blockDim.x) {
+        int64_t e_lo, cnt;
+        row_range(t, q, Q0, Q1, &e_lo, &cnt);
+        if (cnt <= 0) continue;
+        const int64_t pos = base + prefix_to(t, q, Q0, Q1);
+        for (int64_t e = 0; e < cnt; ++e) dst[dest_index(t, q, e_lo + e)] = send[pos + e];
+    }
+}
+
+cudaError_t launch_segment_exchange(int sched, int64_t P, int64_t B, int64_t step, int elem_bytes,
+                                    const int64_t* C, const int64_t* sdispl, const int64_t* rdispl,
+                                    const void* send, void* recv, cudaStream_t st)
+{
+    const unsigned grid = (unsigned)pairs_per_step(sched, P, B);
+    if (elem_bytes == 16)
+        segment_exchange_kernel<uint4><<<grid, 128, 0, st>>>(sched, P, B, step, C, sdispl, rdispl,
+                                                             (const uint4*)send, (uint4*)recv);
+    else
+        segment_exchange_kernel<uint2><<<grid, 128, 0, st>>>(sched, P, B, step, C, sdispl, rdispl,
+                                                             (const uint2*)send, (uint2*)recv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_segment_unpack(const Transpose& t, int sched, int64_t B, int64_t step, int elem_bytes,
+                                  const void* send, void* dst, const int64_t* sbase, cudaStream_t st)
+{
+    const unsigned grid = (unsigned)pairs_per_step(sched, t.src.P, B);
+    if (elem_bytes == 16)
+        segment_unpack_kernel<uint4><<<grid, 128, 0, st>>>(t, sched, B, step, (const uint4*)send, (uint4*)dst, sbase);
+    else
+        segment_unpack_kernel<uint2><<<grid, 128, 0, st>>>(t, sched, B, step, (const uint2*)send, (uint2*)dst, sbase);
+    return cudaGetLastError();
+}
+
 static unsigned grid_for(int64_t N, int sms)
 {
     int64_t want = (N + 255) / 256;
@@ -117,7 +219,8 @@ cudaError_t launch_unpack(const Transpose& t, int elem_bytes, const void* buf, v
 // ------------------------------------------------------------ host tables --
 
 void build_transpose_tables(const Transpose& t, std::vector<int64_t>& C, std::vector<int64_t>& sbase,
-                            std::vector<int64_t>& rbase, std::vector<int64_t>& chunks, int64_t chunk_len)
+                            std::vector<int64_t>& rbase, std::vector<int64_t>& chunks, int64_t chunk_len,
+                            std::vector<int64_t>* sdispl_out, std::vector<int64_t>* rdispl_out)
 {
     const int64_t P = t.src.P;
     C.assign((size_t)(P * P), 0);
@@ -149,6 +252,8 @@ void build_transpose_tables(const Transpose& t, std::vector<int64_t>& C, std::ve
             off += C[(size_t)(r * P + s)];
         }
     }
+    if (sdispl_out) *sdispl_out = sdispl;
+    if (rdispl_out) *rdispl_out = rdispl;
     chunks.clear();
     for (int64_t s = 0; s < P; ++s)
         for (int64_t r = 0; r < P; ++r) {

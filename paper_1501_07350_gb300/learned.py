@@ -114,21 +114,25 @@ def split(rows, held_out=HELD_OUT):
     return train_rows, test_rows
 
 
+TARGET_CAP = 1.0
+ENSEMBLE = 5
+
+
 def arrays(rows):
     """Features and targets of every candidate that ran.
 
-    The target is the candidate's log time minus the mean log time of its
-    problem's candidates: only the order of a problem's candidates matters to
-    the pick, and removing the problem's scale (which spans three decades)
-    lets the network spend its capacity on the differences between candidates."""
+    The target is log(t / t_best of the problem), capped at TARGET_CAP: only
+    the order of a problem's candidates matters to the pick, the problem's
+    own scale (three decades) is removed, and candidates more than e times
+    slower than the best are all just "slow", so the fit spends its capacity
+    on the candidates near the top."""
     X, y = [], []
     for r in rows:
-        lm = [math.log(t) for t in r["ms"] if t > 0]
-        centre = sum(lm) / len(lm)
+        best = math.log(min(t for t in r["ms"] if t > 0))
         for f, t in zip(r["features"], r["ms"]):
             if t > 0:
                 X.append(f)
-                y.append(math.log(t) - centre)
+                y.append(min(math.log(t) - best, TARGET_CAP))
     return np.asarray(X, dtype=np.float32), np.asarray(y, dtype=np.float32)
 
 
@@ -148,22 +152,40 @@ def init_params(d: int, hidden: int, seed: int) -> np.ndarray:
     return p.astype(np.float32)
 
 
-def train(rows, hidden=HIDDEN, steps=8000, lr=3e-3, seed=150107355):
-    """Fit the cost model on the GPU (the library's forward/backward/Adam kernels)."""
+def train(rows, hidden=HIDDEN, steps=8000, lr=3e-3, seed=150107355, members=ENSEMBLE):
+    """Fit an ensemble of cost models on the GPU (the library's forward /
+    backward / Adam kernels), one per seed; returns (list of params, losses of
+    the first member)."""
     X, y = arrays(rows)
     d = X.shape[1]
-    p0 = init_params(d, hidden, seed)
-    p, losses = of.openfft_mlp_train(d, hidden, X, y, steps, lr, p0)
-    return p, losses
+    params, first = [], None
+    for k in range(members):
+        p0 = init_params(d, hidden, seed + k)
+        p, losses = of.openfft_mlp_train(d, hidden, X, y, steps, lr, p0)
+        params.append(p)
+        first = losses if first is None else first
+    return params, first
 
 
 def pick(params, features, hidden=HIDDEN, ms=None):
-    """Candidate of lowest predicted time (skipping those known not to run)."""
+    """Candidate of lowest mean predicted time over the ensemble (skipping
+    candidates known not to run)."""
     F = np.asarray(features, dtype=np.float32)
-    pred = of.openfft_mlp_predict(F.shape[1], hidden, params, F)
+    if not isinstance(params, (list, tuple)):
+        params = [params]
+    pred = np.mean([of.openfft_mlp_predict(F.shape[1], hidden, p, F) for p in params], axis=0)
     if ms is not None:
         pred = np.where(np.asarray(ms) > 0, pred, np.inf)
     return int(np.argmin(pred)), pred
+
+
+def install(path=MODEL_FILE):
+    """Install the committed ensemble for OPENFFT_TUNE_LEARNED."""
+    with open(path) as fh:
+        m = json.load(fh)
+    flat = np.concatenate([np.asarray(p, dtype=np.float32) for p in m["params"]])
+    of.openfft_set_cost_model(m["d"], m["hidden"], flat, count=len(m["params"]))
+    return m
 
 
 def evaluate(rows, params, hidden=HIDDEN):
@@ -212,10 +234,11 @@ def main(argv=None):
     else:
         rows = load_rows(args.data)
         tr, te = split(rows)
-        p, losses = train(tr, steps=args.steps)
-        ev = evaluate(te, p)
-        save({"hidden": HIDDEN, "d": len(tr[0]["features"][0]), "params": [float(v) for v in p],
-              "train_loss": [float(losses[0]), float(losses[-1])], "held_out": summary(ev)}, args.out)
+        ps, losses = train(tr, steps=args.steps)
+        ev = evaluate(te, ps)
+        save({"hidden": HIDDEN, "d": len(tr[0]["features"][0]), "params": [[float(v) for v in p] for p in ps],
+              "target_cap": TARGET_CAP, "train_loss": [float(losses[0]), float(losses[-1])],
+              "held_out": summary(ev), "held_out_problems": ev}, args.out)
         print(json.dumps(summary(ev)))
 
 

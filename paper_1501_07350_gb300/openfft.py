@@ -23,6 +23,10 @@ ERR_TIMEOUT, ERR_ALIAS, ERR_UNSUPPORTED = 6, 7, 8
 C2C_F64, C2C_F32, C2C_SPLIT_BF16, C2C_SPLIT_TF32 = 0, 1, 2, 3
 FORWARD, BACKWARD = -1, 1
 VARIANT_PACK_EXCHANGE_UNPACK, VARIANT_PACK_UNPACK, VARIANT_FUSED = 0, 1, 2
+VARIANT_ISEND_WAITALL, VARIANT_ISEND_WAITALL_BLOCK, VARIANT_ISEND_WAITSOME_BLOCK, VARIANT_SENDRECV = 3, 4, 5, 6
+# the paper's methods (Sec. 3.2.1) by name
+METHODS = {"Alltoallv": 0, "Isend_Waitsome": 1, "fused": 2, "Isend_Waitall": 3, "Isend_Waitall_Block": 4,
+           "Isend_Waitsome_Block": 5, "Sendrecv": 6}
 ARITH_NATIVE, ARITH_DOUBLE_FLOAT = 0, 1
 TUNE_DEFAULT, TUNE_EXHAUSTIVE, TUNE_LEARNED, TUNE_USER = 0, 1, 2, 3
 LAYOUT_ABC, LAYOUT_CAB, LAYOUT_CBA = 0, 1, 2
@@ -101,7 +105,7 @@ def load():
             "openfft_num_features": (i32, []),
             "openfft_candidate_features": (i32, [vp, i32, pf]),
             "openfft_tune_times": (i32, [vp, pf]),
-            "openfft_set_cost_model": (i32, [i32, i32, pf]),
+            "openfft_set_cost_model": (i32, [i32, i32, i32, pf]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -309,12 +313,14 @@ def openfft_tune_times(plan: int) -> np.ndarray:
     return ms
 
 
-def openfft_set_cost_model(d: int, hidden: int, params) -> None:
+def openfft_set_cost_model(d: int, hidden: int, params, count: int = 1) -> None:
+    """Install an ensemble of `count` networks (params: count parameter sets
+    back to back), or remove the model with params=None."""
     if params is None:
-        _check(load().openfft_set_cost_model(d, hidden, None))
+        _check(load().openfft_set_cost_model(0, d, hidden, None))
     else:
         p = _f32(params)
-        _check(load().openfft_set_cost_model(d, hidden, _pf(p)))
+        _check(load().openfft_set_cost_model(count, d, hidden, _pf(p)))
 
 
 # ------------------------------------------------------- convenience ----

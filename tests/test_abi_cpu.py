@@ -150,5 +150,5 @@ def test_committed_learned_data_is_consistent():
     with open(learned.MODEL_FILE) as fh:
         model = json.load(fh)
     assert model["d"] == of.openfft_num_features()
-    assert len(model["params"]) == of.openfft_mlp_num_params(model["d"], model["hidden"])
+    assert all(len(p) == of.openfft_mlp_num_params(model["d"], model["hidden"]) for p in model["params"])
     assert model["held_out"]["mean_regret"] <= 0.05

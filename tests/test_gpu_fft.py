@@ -152,7 +152,8 @@ def test_plane_waves_120x144x160(torch, k0):
 # --------------------------------------------------- transposes alone ----
 
 REDIST = [((4, 3, 2), 3), ((4, 3, 2), 6), ((8, 6, 10), 40), ((12, 10, 9), 30), ((5, 7, 3), 15),
-          ((16, 16, 16), 64), ((32, 32, 32), 4), ((20, 18, 15), 7), ((8, 8, 8), 16), ((7, 1, 5), 5)]
+          ((16, 16, 16), 64), ((32, 32, 32), 4), ((20, 18, 15), 7), ((8, 8, 8), 16), ((7, 1, 5), 5),
+          ((16, 16, 16), 100), ((12, 10, 16), 97)]
 
 
 @pytest.mark.parametrize("shape,P", REDIST)
@@ -166,7 +167,7 @@ def test_transposes_bit_exact(torch, shape, P):
         for which, code in [("abc->cab", 1), ("cab->cba", 2), ("cba->cab", -2), ("cab->abc", -1)]:
             ref, C = oracle.redistribute(Na, Nb, Nc, P, which, src)
             assert np.array_equal(of.openfft_counts(plan, code, P), C)
-            for variant in (of.VARIANT_FUSED, of.VARIANT_PACK_UNPACK, of.VARIANT_PACK_EXCHANGE_UNPACK):
+            for variant in sorted(of.METHODS.values()):           # the six methods of Sec. 3.2.1 and fused
                 xd = torch.from_numpy(src).cuda()
                 yd = torch.full_like(xd, float("nan"))
                 of.openfft_redistribute(plan, code, variant, xd, yd)

@@ -77,7 +77,7 @@ def test_learned_mode_follows_the_model(lib):
     p[o:o + d * H] = W1.ravel(); o += d * H + H
     p[o:o + H * H] = W2.ravel(); o += H * H + H
     p[o] = -1.0
-    of.openfft_set_cost_model(d, H, p)
+    of.openfft_set_cost_model(d, H, p, count=1)
     try:
         h = of.openfft_plan(48, 64, 40, 8, of.C2C_F64)
         try:
@@ -100,10 +100,22 @@ def test_trained_model_regret_on_held_out_problems(lib):
     rows = learned.load_rows()
     train_rows, test_rows = learned.split(rows)
     assert len(test_rows) == len(learned.HELD_OUT)
-    p, losses = learned.train(train_rows)
+    ps, losses = learned.train(train_rows)
     assert losses[-1] < 0.05 * losses[0]
-    ev = learned.evaluate(test_rows, p)
+    ev = learned.evaluate(test_rows, ps)
     s = learned.summary(ev)
     assert s["mean_regret"] <= 0.05, s
     assert s["geomean_speedup_vs_default"] >= 0.97, s
     assert s["tuning_cost_avoided_ms"] > 0
+    # the committed ensemble, installed, drives OPENFFT_TUNE_LEARNED
+    learned.install()
+    try:
+        h = of.openfft_plan(256, 256, 256, 64, of.C2C_F64)
+        try:
+            of.openfft_set_tuning(h, of.TUNE_LEARNED)
+            c = of.openfft_candidate(h, of.openfft_current_candidate(h))
+            assert c["variant"] == of.VARIANT_FUSED
+        finally:
+            of.openfft_destroy(h)
+    finally:
+        of.openfft_set_cost_model(0, 0, None)
