@@ -259,6 +259,17 @@ int openfft_tune_times(openfft_plan_t plan, float* ms);
  * parameters are copied. */
 int openfft_set_cost_model(int count, int d, int hidden, const float* params);
 
+/* ------------------------------------------------ tensor-core GEMM ----- */
+
+/* Split-precision GEMM on the tcgen05 tensor cores, the contraction of the
+ * DFT-GEMM form: D[M][N] = A[M][K] B[N][K]^T with fp32 host arrays.  Each
+ * operand is split into a high part (tf32 if tf32 != 0, else bf16) and the
+ * rounded remainder; with split != 0 D accumulates A_hi B_hi + A_hi B_lo +
+ * A_lo B_hi in fp32 (without split, A_hi B_hi only).  N in {16, 32, 48, 64},
+ * K a multiple of 8 (tf32) or 16 (bf16) up to 64, any M.  Copies to and from
+ * the device and waits. */
+int openfft_tc_gemm(int tf32, int split, int M, int N, int K, const float* A, const float* B, float* D);
+
 /* One transpose alone (for testing the permutation): `in` holds the source
  * ordering, `out` receives the destination ordering, bit for bit.
  * exchange as in openfft_counts; variant: OPENFFT_VARIANT_*. */

@@ -1,0 +1,140 @@
+// tc.cuh -- fifth-generation tensor core (tcgen05) building blocks: tensor
+// memory allocation, shared-memory operand descriptors, instruction
+// descriptors, MMA issue and completion, tensor-memory loads.
+//
+// Operands are staged in shared memory in the canonical K-major layout
+// without swizzle: "core matrices" of 8 rows x 16 bytes (128 contiguous
+// bytes, row r at byte 16 r); core matrix (row group i, K group kk) of a tile
+// with KT K groups sits at byte (i * KT + kk) * 128, so core matrices adjacent
+// in K are 128 bytes apart (leading byte offset) and those adjacent in M/N
+// are KT * 128 bytes apart (stride byte offset).  One MMA consumes 32 bytes
+// of K (two core matrices): 8 tf32 or 16 bf16 values.
+//
+// The accumulator D (M = 128 rows, fp32) lives in tensor memory: row i in
+// lane i, column j in column base + j.  Warp w of the CTA reads lanes
+// 32 (w % 4) .. 32 (w % 4) + 31 with tcgen05.ld.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ofg {
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// ---------------------------------------------------------- tensor memory --
+// One full warp allocates `ncols` (power of two >= 32) columns and writes the
+// tensor-memory address to *dst; the same warp frees them.
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                 :: "r"(smem_u32(dst)), "r"(ncols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(taddr), "r"(ncols) : "memory");
+}
+
+// ------------------------------------------------------------ descriptors --
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo_bytes >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo_bytes >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;          // descriptor version of tcgen05
+    return d;                        // base offset 0, no swizzle
+}
+
+// Instruction descriptor: D fp32, A and B of the same type (tf32: 2, bf16: 1),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc(uint32_t ab_type, int M, int N)
+{
+    return (1u << 4) | (ab_type << 7) | (ab_type << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+constexpr uint32_t kTypeBF16 = 1, kTypeTF32 = 2;
+
+// ------------------------------------------------------------------- MMA ---
+// D (+)= A x B^T for one 32-byte K slice; issued by one thread.
+template <bool TF32>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t id, uint32_t accumulate)
+{
+    if (TF32)
+        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                     :: "r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(id), "r"(accumulate) : "memory");
+    else
+        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                     :: "r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(id), "r"(accumulate) : "memory");
+}
+
+// arrive on the mbarrier once every MMA issued so far by this thread is complete
+__device__ __forceinline__ void commit(uint64_t* mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                 :: "r"(smem_u32(mbar)) : "memory");
+}
+
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+// generic-proxy shared-memory writes -> visible to the tensor core (async proxy)
+__device__ __forceinline__ void fence_smem_to_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// -------------------------------------------------------------- mbarrier ---
+__device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(smem_u32(m)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* m, uint32_t phase)
+{
+    uint32_t ok;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(smem_u32(m)), "r"(phase) : "memory");
+    return ok != 0;
+}
+// Bounded wait for `phase` of the mbarrier: false if `budget` clock cycles pass first.
+__device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t phase, long long budget)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(m, phase))
+        if (clock64() - t0 > budget) return false;
+    return true;
+}
+
+// ------------------------------------------------------ tensor-memory load --
+// 16 consecutive fp32 columns of this thread's lane.
+__device__ __forceinline__ void ld16(uint32_t taddr, float* v)
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr) : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ------------------------------------------------------------ operands ----
+// Byte offset of element (row, k) in a K-major no-swizzle tile with KT K
+// groups; esize 4 (tf32) or 2 (bf16).
+__host__ __device__ __forceinline__ uint32_t op_offset(int row, int k, int KT, int esize)
+{
+    const int per16 = 16 / esize;
+    return (uint32_t)(((row >> 3) * KT + (k / per16)) * 128 + (row & 7) * 16 + (k % per16) * esize);
+}
+
+// Split x into hi + lo: tf32 keeps 10 fraction bits (round to nearest), bf16 7.
+__device__ __forceinline__ float round_tf32(float x)
+{
+    uint32_t b = __float_as_uint(x);
+    b = (b + 0x1000u) & 0xFFFFE000u;          // round half up on the 13 dropped bits
+    return __uint_as_float(b);
+}
+
+}  // namespace tc
+}  // namespace ofg

@@ -42,6 +42,7 @@ EXPORTS = [
     "openfft_plan_many", "openfft_exec_many", "openfft_batch_debug",
     "openfft_mlp_num_params", "openfft_mlp_predict", "openfft_mlp_loss_grad", "openfft_mlp_train",
     "openfft_num_features", "openfft_candidate_features", "openfft_tune_times", "openfft_set_cost_model",
+    "openfft_tc_gemm",
 ]
 
 _lock = threading.Lock()
@@ -106,6 +107,7 @@ def load():
             "openfft_candidate_features": (i32, [vp, i32, pf]),
             "openfft_tune_times": (i32, [vp, pf]),
             "openfft_set_cost_model": (i32, [i32, i32, i32, pf]),
+            "openfft_tc_gemm": (i32, [i32, i32, i32, i32, i32, pf, pf, pf]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -321,6 +323,16 @@ def openfft_set_cost_model(d: int, hidden: int, params, count: int = 1) -> None:
     else:
         p = _f32(params)
         _check(load().openfft_set_cost_model(count, d, hidden, _pf(p)))
+
+
+def openfft_tc_gemm(A, B, tf32: bool = True, split: bool = True) -> np.ndarray:
+    """D = A B^T on the tensor cores (split precision, fp32 accumulation)."""
+    A, B = _f32(A), _f32(B)
+    M, K = A.shape
+    N = B.shape[0]
+    D = np.empty((M, N), dtype=np.float32)
+    _check(load().openfft_tc_gemm(1 if tf32 else 0, 1 if split else 0, M, N, K, _pf(A), _pf(B), _pf(D)))
+    return D
 
 
 # ------------------------------------------------------- convenience ----
