@@ -372,6 +372,8 @@ def measure_forms(of, torch, plans_f64, x, y, z, n, stream, args):
     # transforms run one plan at a time in FP64 and in FP32
     if not args.no_batch:
         out["batch64"] = measure_batch(of, torch, stream)
+    # non-power-of-two 120 x 144 x 160, P = 32: FP64 vs FP32 vs split tensor-core forms
+    out["mixed_120x144x160"] = measure_mixed(of, torch, stream)
     # 512^3 forward, FP64, P = 1024 (the large configuration)
     if not args.no_512:
         n5 = 512
@@ -391,6 +393,92 @@ def measure_forms(of, torch, plans_f64, x, y, z, n, stream, args):
         of.openfft_destroy(h5)
         del xb, yb
         torch.cuda.empty_cache()
+    return out
+
+
+def measure_mixed(of, torch, stream, reps=7):
+    """Non-power-of-two 120 x 144 x 160 at P = 32: FP64 (native and double-float,
+    each its best candidate), FP32, and the split tf32 / bf16 tensor-core
+    DFT-GEMM forms, per forward transform.  The complex128 array (44 MB) fits
+    in L2, so a 256 MiB buffer is written between timed reps.  Errors are
+    against the FP64 result on the same seeded uniform[-1,1) input (complex64
+    for the reduced forms) and, for a plane wave, against its closed form."""
+    from paper_1501_07350_gb300 import synth
+    Na, Nb, Nc, P = 120, 144, 160, 32
+    N = Na * Nb * Nc
+    dev = torch.device("cuda", torch.cuda.current_device())
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    x64 = torch.from_numpy(synth.complex_field((N,), seed=synth.config_seed(3))).to(dev)
+    x32 = x64.to(torch.complex64)
+    k0 = (59, 71, 79)
+    pw = torch.from_numpy(synth.plane_wave(Na, Nb, Nc, k0).reshape(-1)).to(dev)
+
+    def timed(h, a, b):
+        for _ in range(3):
+            of.openfft_exec_c2c(h, a, b, of.FORWARD)
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            of.openfft_exec_c2c(h, a, b, of.FORWARD)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        of.openfft_sync(h)
+        return statistics.median(ts)
+
+    def rel(a, b):
+        return float(torch.linalg.vector_norm(a.to(torch.complex128) - b) / torch.linalg.vector_norm(b))
+
+    def plane_wave_err(h, dt):
+        y = torch.empty_like(pw, dtype=dt)
+        of.openfft_exec_c2c(h, pw.to(dt), y, of.FORWARD)
+        of.openfft_sync(h)
+        y = y.to(torch.complex128)
+        # forward output is cba-ordered: (kc, kb, ka) -> index (kc * Nb + kb) * Na + ka
+        idx = (k0[2] * Nb + k0[1]) * Na + k0[0]
+        y[idx] -= N
+        return float(torch.linalg.vector_norm(y)) / (N * math.sqrt(N))
+
+    peak = load_peaks()[0]
+    out = {"shape": [Na, Nb, Nc], "P": P, "l2": "256 MiB written between reps"}
+    h = of.openfft_plan(Na, Nb, Nc, P, of.C2C_F64)
+    of.openfft_set_stream(h, stream)
+    ref = torch.empty_like(x64)
+    for arith, name in [(of.ARITH_NATIVE, "f64_native"), (of.ARITH_DOUBLE_FLOAT, "f64_doublefloat")]:
+        best = None
+        for ci in range(of.openfft_num_candidates(h)):
+            c = of.openfft_candidate(h, ci)
+            if c["arith"] != arith or c["variant"] != of.VARIANT_FUSED:
+                continue
+            of.openfft_set_tuning(h, of.TUNE_USER, ci)
+            ms = timed(h, x64, ref)
+            if best is None or ms < best[0]:
+                best = (ms, c)
+        out[name] = {"ms": round(best[0], 4), "gflops": round(flops(N) / best[0] / 1e6, 1),
+                     "hbm_frac": round(6 * N * 16 / (best[0] * 1e-3) / 1e9 / peak, 4), "chosen": best[1]}
+    of.openfft_set_tuning(h, of.TUNE_USER, [i for i in range(of.openfft_num_candidates(h))
+                                            if of.openfft_candidate(h, i)["arith"] == of.ARITH_NATIVE][0])
+    of.openfft_exec_c2c(h, x64, ref, of.FORWARD)
+    of.openfft_sync(h)
+    out["f64_native"]["plane_wave_err"] = plane_wave_err(h, torch.complex128)
+    of.openfft_destroy(h)
+    for dtype, name, bound in [(of.C2C_F32, "f32", 1e-5), (of.C2C_SPLIT_TF32, "split_tf32_tc", 1e-5),
+                               (of.C2C_SPLIT_BF16, "split_bf16_tc", 1e-4)]:
+        h = of.openfft_plan(Na, Nb, Nc, P, dtype)
+        of.openfft_set_stream(h, stream)
+        of.openfft_set_tuning(h, of.TUNE_EXHAUSTIVE)
+        y = torch.empty_like(x32)
+        ms = timed(h, x32, y)
+        out[name] = {"ms": round(ms, 4), "gflops": round(flops(N) / ms / 1e6, 1),
+                     "hbm_frac": round(6 * N * 8 / (ms * 1e-3) / 1e9 / peak, 4),
+                     "rel_l2_vs_f64": rel(y, ref), "plane_wave_err": plane_wave_err(h, torch.complex64),
+                     "bound": bound, "chosen": of.openfft_candidate(h, of.openfft_current_candidate(h))}
+        of.openfft_destroy(h)
+    del flush
+    torch.cuda.empty_cache()
     return out
 
 
@@ -520,12 +608,14 @@ def run_single(args, local_rank):
     stream = torch.cuda.current_stream()
     shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else (args.n,) * 3
     N = shape[0] * shape[1] * shape[2]
-    dtype = of.C2C_F32 if args.form == "f32" else of.C2C_F64
-    want_arith = of.ARITH_DOUBLE_FLOAT if args.form == "f64-df" else of.ARITH_NATIVE
+    dtype = {"f32": of.C2C_F32, "tf32": of.C2C_SPLIT_TF32, "bf16": of.C2C_SPLIT_BF16}.get(args.form, of.C2C_F64)
+    want_arith = {"f64-df": of.ARITH_DOUBLE_FLOAT, "tf32": of.ARITH_TC_TF32,
+                  "bf16": of.ARITH_TC_BF16}.get(args.form, of.ARITH_NATIVE)
+    tc_form = want_arith in (of.ARITH_TC_TF32, of.ARITH_TC_BF16)
     want_variant = {"fused": of.VARIANT_FUSED, "v1": of.VARIANT_PACK_UNPACK,
                     "v0": of.VARIANT_PACK_EXCHANGE_UNPACK}[args.variant]
     x = torch.from_numpy(synth.complex_field((N,), seed=synth.config_seed(2))).cuda()
-    if dtype == of.C2C_F32:
+    if dtype != of.C2C_F64:
         x = x.to(torch.complex64)
     y = torch.empty_like(x)
     h = of.openfft_plan(shape[0], shape[1], shape[2], args.P, dtype)
@@ -533,7 +623,9 @@ def run_single(args, local_rank):
     pick = None
     for ci in range(of.openfft_num_candidates(h)):
         c = of.openfft_candidate(h, ci)
-        if (c["variant"] == want_variant and c["arith"] == want_arith and c["lines_per_cta"] == args.G
+        if tc_form and c["arith"] == want_arith and pick is None:
+            pick = ci
+        elif (c["variant"] == want_variant and c["arith"] == want_arith and c["lines_per_cta"] == args.G
                 and (want_variant != of.VARIANT_FUSED
                      or c["kernel"] == {"auto": 0, "warp": 0, "tile": 2, "generic": 3}[args.kernel])):
             pick = ci
@@ -551,7 +643,7 @@ def run_single(args, local_rank):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    E = 8 if dtype == of.C2C_F32 else 16
+    E = 16 if dtype == of.C2C_F64 else 8
     print(json.dumps({"single": args.form, "shape": list(shape), "P": args.P, "variant": args.variant,
                       "G": args.G, "kernel": args.kernel,
                       "ms": round(ms, 4), "gflops": round(flops(N) / ms / 1e6, 1),
@@ -570,10 +662,12 @@ def main():
     ap.add_argument("--no-512", dest="no_512", action="store_true", help="skip the 512^3 form")
     ap.add_argument("--no-batch", dest="no_batch", action="store_true", help="skip the batched form")
     ap.add_argument("--only-batch", dest="only_batch", action="store_true", help="time the batched form only")
+    ap.add_argument("--only-mixed", dest="only_mixed", action="store_true",
+                    help="time the 120x144x160 FP64 / FP32 / split tensor-core forms only")
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
     ap.add_argument("--single", action="store_true",
                     help="time one form on one n^3 shape (forward only), for profiling")
-    ap.add_argument("--form", choices=["f64-native", "f64-df", "f32"], default="f64-df")
+    ap.add_argument("--form", choices=["f64-native", "f64-df", "f32", "tf32", "bf16"], default="f64-df")
     ap.add_argument("--variant", choices=["fused", "v1", "v0"], default="fused")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--shape", default="", help="Na,Nb,Nc (overrides --n)")
@@ -598,6 +692,14 @@ def main():
         _build.build()
         torch.cuda.set_device(local_rank)
         print(json.dumps({"batch64": measure_batch(of, torch, torch.cuda.current_stream())}))
+        return
+    if args.only_mixed:
+        import torch
+        from paper_1501_07350_gb300 import _build
+        from paper_1501_07350_gb300 import openfft as of
+        _build.build()
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"mixed_120x144x160": measure_mixed(of, torch, torch.cuda.current_stream())}))
         return
     if world > 1:
         import torch

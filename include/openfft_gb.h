@@ -49,8 +49,8 @@ typedef struct openfft_plan_s* openfft_plan_t;
 enum {
     OPENFFT_C2C_F64 = 0,        /* complex128 in/out, FP64-accurate (<= 1e-12 rel. L2)   */
     OPENFFT_C2C_F32 = 1,        /* complex64 in/out, FP32 arithmetic                     */
-    OPENFFT_C2C_SPLIT_BF16 = 2, /* complex64 in/out, tensor-core DFT-GEMM, bf16 hi/lo    */
-    OPENFFT_C2C_SPLIT_TF32 = 3  /* complex64 in/out, tensor-core DFT-GEMM, tf32 hi/lo    */
+    OPENFFT_C2C_SPLIT_BF16 = 2, /* complex64 in/out, tensor-core DFT-GEMM, bf16 hi/lo (<= 1e-4) */
+    OPENFFT_C2C_SPLIT_TF32 = 3  /* complex64 in/out, tensor-core DFT-GEMM, tf32 hi/lo (<= 1e-5) */
 };
 
 /* Sign of the exponent. */
@@ -106,6 +106,12 @@ enum {
  *   (about 48 significant bits; finite inputs with |x| < 2^90 and outputs
  *   below 2^126).  Both meet the FP64 bound of 1e-12 relative L2. */
 enum { OPENFFT_ARITH_NATIVE = 0, OPENFFT_ARITH_DOUBLE_FLOAT = 1 };
+/* Arithmetic of the split-precision plans (OPENFFT_C2C_SPLIT_TF32 / _BF16):
+ * every axis n = R S (2 <= R, S <= 32) is transformed by two tensor-core
+ * GEMM passes with the R- and S-point DFT matrices, operands split into a
+ * high part and the rounded remainder, fp32 accumulation (stated bounds:
+ * 1e-5 relative L2 for tf32, 1e-4 for bf16). */
+enum { OPENFFT_ARITH_TC_TF32 = 2, OPENFFT_ARITH_TC_BF16 = 3 };
 
 /* Tuning modes of openfft_set_tuning (Sec. 3.2.3: auto-tuning on, off = the
  * default method, or a user-selected method). */

@@ -119,13 +119,16 @@ struct openfft_plan_s {
     double t_ms[4] = {0, 0, 0, 0};
     int64_t t_launch[4] = {0, 0, 0, 0};
     BatchPlan* batch = nullptr;   // set for plans made by openfft_plan_many
+    int* d_status = nullptr;      // device status word of the tensor-core stages
+    void* bimg[3] = {};           // DFT-GEMM operand images per axis (split dtypes)
 };
 
 namespace {
 
 int tix_of(int which) { return which == 1 ? 0 : (which == 2 ? 1 : (which == -2 ? 2 : 3)); }
 
-int elem_bytes_of(int arith) { return arith == ARITH_F32 ? 8 : 16; }
+int elem_bytes_of(int arith) { return (arith == ARITH_F64 || arith == ARITH_DF) ? 16 : 8; }
+bool is_tc(int arith) { return arith == ARITH_TC_TF32 || arith == ARITH_TC_BF16; }
 
 // Build the launch of one stage: lines of length n; l = i1 + i2*M1;
 // out(l,k) = i1*S1 + i2*S2 + k*Sk.
@@ -136,6 +139,32 @@ int make_stage(openfft_plan_s* p, int axis, int arith, int Gt, int family, int64
     const int n = axis == 0 ? p->Na : (axis == 1 ? p->Nb : p->Nc);
     const std::vector<int>& rad = p->rad[axis];
     const int E = elem_bytes_of(arith);
+    if (is_tc(arith) && do_fft) {
+        // DFT-GEMM stage: n = R S, tiles of Gt lines (as many as fit)
+        int R = 0, S = 0;
+        if (!dftgemm_factor(n, arith == ARITH_TC_TF32, &R, &S))
+            return fail(OPENFFT_ERR_UNSUPPORTED_RADIX, "DFT-GEMM form: every axis must be R*S with 2 <= R, S <= 32");
+        int G = dftgemm_lines(n, R, S, arith == ARITH_TC_TF32, Gt);
+        if (!G) return fail(OPENFFT_ERR_UNSUPPORTED_RADIX, "DFT-GEMM form: axis too long for one CTA");
+        if (!p->bimg[axis]) return fail(OPENFFT_ERR_INVALID_ARG, "DFT-GEMM form: plan has no operand image");
+        const int64_t Mg = group_i2 ? M2 : M1;
+        StageArgs& a = L.args;
+        std::memset(&a, 0, sizeof(a));
+        a.tw = p->tw[axis][FMT_C64];
+        a.aux = p->bimg[axis];
+        a.M1 = M1; a.M2 = M2; a.S1 = S1; a.S2 = S2; a.Sk = Sk;
+        a.ngroups = (Mg + G - 1) / G;
+        a.scale = scale;
+        a.n = n; a.G = G; a.log2G = ilog2(G);
+        a.group_i2 = group_i2; a.contig_store = contig;
+        a.npass = 2; a.radix[0] = R; a.radix[1] = S;
+        a.conj_in = conj_in; a.conj_out = conj_out; a.do_fft = 1;
+        a.in_fmt = in_fmt; a.out_fmt = out_fmt;
+        L.arith = arith; L.sms = p->sms; L.family = family; L.status = p->d_status;
+        L.grid = a.ngroups * (group_i2 ? M1 : M2);
+        L.smem = 0;
+        return OPENFFT_OK;
+    }
     const size_t cap = 200 * 1024;
     int G = Gt;
     const int64_t Mg = group_i2 ? M2 : M1;
@@ -145,7 +174,7 @@ int make_stage(openfft_plan_s* p, int axis, int arith, int Gt, int family, int64
     StageArgs& a = L.args;
     std::memset(&a, 0, sizeof(a));
     a.in = nullptr; a.out = nullptr;
-    const int twf = arith == ARITH_F64 ? FMT_C128 : (arith == ARITH_F32 ? FMT_C64 : FMT_DF);
+    const int twf = arith == ARITH_F64 ? FMT_C128 : ((arith == ARITH_F32 || is_tc(arith)) ? FMT_C64 : FMT_DF);
     a.tw = p->tw[axis][twf];
     a.M1 = M1; a.M2 = M2; a.S1 = S1; a.S2 = S2; a.Sk = Sk;
     a.ngroups = (Mg + G - 1) / G;
@@ -233,8 +262,8 @@ int build_ops(openfft_plan_s* p, const Candidate& c)
 {
     const int64_t Na = p->Na, Nb = p->Nb, Nc = p->Nc, N = p->N;
     const int ar = c.arith;
-    const int ext = ar == ARITH_F32 ? FMT_C64 : FMT_C128;     // user arrays
-    const int mid = ar == ARITH_DF ? FMT_DF : ext;            // workspace arrays
+    const int ext = (ar == ARITH_F32 || is_tc(ar)) ? FMT_C64 : FMT_C128;   // user arrays
+    const int mid = ar == ARITH_DF ? FMT_DF : ext;                          // workspace arrays
     const double invN = 1.0 / (double)N;
     std::vector<Op>& F = p->ops_fwd;
     std::vector<Op>& B = p->ops_bwd;
@@ -392,11 +421,13 @@ void free_plan(openfft_plan_s* p)
     if (!p) return;
     cudaFree(p->bufA); cudaFree(p->bufB);
     for (auto& row : p->tw) for (void* t : row) cudaFree(t);
+    for (void* b : p->bimg) cudaFree(b);
     for (auto& T : p->tt) {
         cudaFree(T.d_sbase); cudaFree(T.d_rbase); cudaFree(T.d_chunks);
         cudaFree(T.d_C); cudaFree(T.d_sdispl); cudaFree(T.d_rdispl);
     }
     cudaFree(p->stage_in); cudaFree(p->stage_out);
+    cudaFree(p->d_status);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
     if (p->batch) batch_destroy(p->batch);
     delete p;
@@ -466,7 +497,7 @@ int g_model_d = 0, g_model_h = 0, g_model_k = 0;
 // buffers and keep the faster run; the current selection is restored.
 int time_candidates(openfft_plan_s* p, std::vector<float>& ms)
 {
-    const size_t bytes = (size_t)p->N * (p->dtype == OPENFFT_C2C_F32 ? 8 : 16);
+    const size_t bytes = (size_t)p->N * p->elem_bytes;
     void *tin = nullptr, *tout = nullptr;
     if (cudaMalloc(&tin, bytes) || cudaMalloc(&tout, bytes)) {
         cudaGetLastError(); cudaFree(tin);
@@ -538,13 +569,11 @@ int openfft_decomp_counts(int Na, int Nb, int Nc, int P, int exchange, int64_t* 
 openfft_plan_t openfft_plan(int Na, int Nb, int Nc, int P, int dtype)
 {
     if (validate_dims(Na, Nb, Nc, P)) return nullptr;
-    if (dtype != OPENFFT_C2C_F64 && dtype != OPENFFT_C2C_F32) {
-        if (dtype == OPENFFT_C2C_SPLIT_BF16 || dtype == OPENFFT_C2C_SPLIT_TF32)
-            fail(OPENFFT_ERR_UNSUPPORTED, "split-precision plans are created by openfft_plan with a supported build");
-        else
-            fail(OPENFFT_ERR_INVALID_ARG, "unknown dtype");
+    if (dtype < OPENFFT_C2C_F64 || dtype > OPENFFT_C2C_SPLIT_TF32) {
+        fail(OPENFFT_ERR_INVALID_ARG, "unknown dtype");
         return nullptr;
     }
+    const bool c64 = dtype != OPENFFT_C2C_F64;             // complex64 data
     openfft_plan_s* p = new openfft_plan_s();
     p->Na = Na; p->Nb = Nb; p->Nc = Nc; p->P = P; p->dtype = dtype;
     p->N = (int64_t)Na * Nb * Nc;
@@ -559,7 +588,7 @@ openfft_plan_t openfft_plan(int Na, int Nb, int Nc, int P, int dtype)
     if ((e = cudaGetDevice(&p->device))) { cuda_fail(e, "cudaGetDevice"); delete p; return nullptr; }
     cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
     if ((e = stage_kernels_init(200 * 1024))) { cuda_fail(e, "kernel attributes"); delete p; return nullptr; }
-    p->elem_bytes = dtype == OPENFFT_C2C_F32 ? 8 : 16;
+    p->elem_bytes = c64 ? 8 : 16;
     const size_t bytes = (size_t)p->N * p->elem_bytes;
     if (cudaMalloc(&p->bufA, bytes) || cudaMalloc(&p->bufB, bytes)) {
         cudaGetLastError();
@@ -569,7 +598,7 @@ openfft_plan_t openfft_plan(int Na, int Nb, int Nc, int P, int dtype)
     }
     // twiddle tables (FP64 sincospi on the device)
     for (int ax = 0; ax < 3; ++ax) {
-        const int fmts[2] = {dtype == OPENFFT_C2C_F32 ? FMT_C64 : FMT_C128, dtype == OPENFFT_C2C_F32 ? -1 : FMT_DF};
+        const int fmts[2] = {c64 ? FMT_C64 : FMT_C128, c64 ? -1 : FMT_DF};
         for (int f : fmts) {
             if (f < 0) continue;
             const size_t eb = f == FMT_C64 ? 8 : 16;
@@ -580,6 +609,24 @@ openfft_plan_t openfft_plan(int Na, int Nb, int Nc, int P, int dtype)
                 return nullptr;
             }
             if ((e = launch_twiddles(lens[ax], f, p->tw[ax][f], nullptr))) { cuda_fail(e, "twiddles"); free_plan(p); return nullptr; }
+        }
+    }
+    // operand images of the DFT-GEMM stages (split dtypes; an axis that does
+    // not factor keeps none and the plan is refused when its stages are built)
+    if (dtype == OPENFFT_C2C_SPLIT_TF32 || dtype == OPENFFT_C2C_SPLIT_BF16) {
+        const bool tf32 = dtype == OPENFFT_C2C_SPLIT_TF32;
+        for (int ax = 0; ax < 3; ++ax) {
+            int R = 0, S = 0;
+            if (!dftgemm_factor(lens[ax], tf32, &R, &S)) continue;
+            if (cudaMalloc(&p->bimg[ax], dftgemm_image_bytes(lens[ax], R, S, tf32))) {
+                cudaGetLastError();
+                fail(OPENFFT_ERR_NOMEM, "operand image allocation failed");
+                free_plan(p);
+                return nullptr;
+            }
+            if ((e = launch_dftgemm_image(lens[ax], R, S, tf32, p->tw[ax][FMT_C64], p->bimg[ax], nullptr))) {
+                cuda_fail(e, "operand image"); free_plan(p); return nullptr;
+            }
         }
     }
     // transpose tables for the explicit variants
@@ -606,6 +653,12 @@ openfft_plan_t openfft_plan(int Na, int Nb, int Nc, int P, int dtype)
         cudaMemcpy(T.d_sdispl, sd.data(), pp, cudaMemcpyHostToDevice);
         cudaMemcpy(T.d_rdispl, rd.data(), pp, cudaMemcpyHostToDevice);
     }
+    if (cudaMalloc(&p->d_status, sizeof(int)) || cudaMemset(p->d_status, 0, sizeof(int))) {
+        cudaGetLastError();
+        fail(OPENFFT_ERR_NOMEM, "status word");
+        free_plan(p);
+        return nullptr;
+    }
     if ((e = cudaDeviceSynchronize())) { cuda_fail(e, "plan setup"); free_plan(p); return nullptr; }
     // candidates (Sec. 3.2.3: the set the tuner chooses from).  The fused
     // variant is tried with every stage-kernel family and tile width; the six
@@ -614,10 +667,16 @@ openfft_plan_t openfft_plan(int Na, int Nb, int Nc, int P, int dtype)
     {
         std::vector<int> ariths;
         if (dtype == OPENFFT_C2C_F32) ariths = {ARITH_F32};
+        else if (dtype == OPENFFT_C2C_SPLIT_TF32) ariths = {ARITH_TC_TF32};
+        else if (dtype == OPENFFT_C2C_SPLIT_BF16) ariths = {ARITH_TC_BF16};
         else ariths = {ARITH_DF, ARITH_F64};
-        const bool f32 = dtype == OPENFFT_C2C_F32;
+        const bool f32 = c64;
         const int gw = f32 ? 16 : 8, gn = f32 ? 8 : 4;
         for (int ar : ariths) {
+            if (is_tc(ar)) {               // the DFT-GEMM form: fused stores only, tiles of 8 / 16 / 4 lines
+                for (int g : {8, 16, 4}) p->cands.push_back(Candidate{OPENFFT_VARIANT_FUSED, ar, g, KERNEL_AUTO});
+                continue;
+            }
             p->cands.push_back(Candidate{OPENFFT_VARIANT_FUSED, ar, gw, KERNEL_AUTO});
             p->cands.push_back(Candidate{OPENFFT_VARIANT_FUSED, ar, gn, KERNEL_AUTO});
             p->cands.push_back(Candidate{OPENFFT_VARIANT_FUSED, ar, gw, KERNEL_TILE});
@@ -662,7 +721,7 @@ int openfft_exec_c2c(openfft_plan_t plan, const void* in, void* out, int dir)
 int openfft_exec_c2c_host(openfft_plan_t plan, const void* host_in, void* host_out, int dir)
 {
     if (!plan || !host_in || !host_out) return fail(OPENFFT_ERR_INVALID_ARG, "null plan or buffer");
-    const size_t bytes = (size_t)plan->N * (plan->dtype == OPENFFT_C2C_F32 ? 8 : 16);
+    const size_t bytes = (size_t)plan->N * plan->elem_bytes;
     if (!plan->stage_in) {
         if (cudaMalloc(&plan->stage_in, bytes) || cudaMalloc(&plan->stage_out, bytes)) {
             cudaGetLastError();
@@ -688,6 +747,14 @@ int openfft_sync(openfft_plan_t plan)
     }
     cudaError_t e = cudaStreamSynchronize(plan->stream);
     if (e) return cuda_fail(e, "stream synchronize");
+    int st = 0;
+    if (plan->d_status) {
+        if ((e = cudaMemcpy(&st, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost))) return cuda_fail(e, "status word");
+        if (st) {
+            cudaMemset(plan->d_status, 0, sizeof(int));
+            return fail(st, "a bounded tensor-core completion wait ran out");
+        }
+    }
     return OPENFFT_OK;
 }
 
@@ -717,7 +784,9 @@ int openfft_candidate(openfft_plan_t plan, int index, int* variant, int* arith, 
     if (!plan || index < 0 || index >= (int)plan->cands.size()) return fail(OPENFFT_ERR_INVALID_ARG, "bad candidate");
     const Candidate& c = plan->cands[(size_t)index];
     if (variant) *variant = c.variant;
-    if (arith) *arith = c.arith == ARITH_DF ? OPENFFT_ARITH_DOUBLE_FLOAT : OPENFFT_ARITH_NATIVE;
+    if (arith) *arith = c.arith == ARITH_DF ? (int)OPENFFT_ARITH_DOUBLE_FLOAT
+                      : (c.arith == ARITH_TC_TF32 ? (int)OPENFFT_ARITH_TC_TF32
+                      : (c.arith == ARITH_TC_BF16 ? (int)OPENFFT_ARITH_TC_BF16 : (int)OPENFFT_ARITH_NATIVE));
     if (lines_per_cta) *lines_per_cta = c.G;
     if (kernel) *kernel = c.family;
     return OPENFFT_OK;
@@ -874,7 +943,7 @@ int openfft_redistribute(openfft_plan_t plan, int exchange, int variant, const v
         return fail(OPENFFT_ERR_INVALID_ARG, "exchange must be 1, 2, -2 or -1");
     const int64_t Na = plan->Na, Nb = plan->Nb, Nc = plan->Nc;
     const int E = (int)plan->elem_bytes;
-    const int ar = plan->dtype == OPENFFT_C2C_F32 ? ARITH_F32 : ARITH_F64;
+    const int ar = plan->elem_bytes == 8 ? ARITH_F32 : ARITH_F64;
     const int fmt = ar == ARITH_F32 ? FMT_C64 : FMT_C128;
     const TransposeTables& T = plan->tt[tix_of(exchange)];
     cudaError_t e = cudaSuccess;

@@ -1,0 +1,456 @@
+// dftgemm.cu -- FFT stage whose small DFT blocks are dense complex GEMMs on
+// the tcgen05 tensor cores, in split precision (the precision forms
+// OPENFFT_C2C_SPLIT_TF32 / OPENFFT_C2C_SPLIT_BF16, complex64 data).
+//
+// A line of length n = R S is transformed in two GEMM passes (four-step):
+//   pass 1, rows (g, t), t < S:  Y[t][q] = sum_{j<R} x[t + S j] W_R^{j q}       (q < R)
+//   pass 2, rows (g, k), k < R:  Z[k + R q] = sum_{j<S} (W_n^{j k} Y[j][k]) W_S^{j q}   (q < S)
+// which is the DFT of x in natural order (the Stockham steps with radices R
+// and S).  Each pass is D = A B^T with the complex data real-ified and
+// interleaved: A row = (re x_0, im x_0, re x_1, ...), and B[2q][2j] = c,
+// B[2q][2j+1] = s, B[2q+1][2j] = -s, B[2q+1][2j+1] = c for W^{jq} = c - i s.
+// Both operands are split into a high part (tf32 or bf16) and the rounded
+// remainder; D = A_hi B_hi + A_hi B_lo + A_lo B_hi accumulates in fp32 in
+// tensor memory.  K and N are padded with zeros to the MMA granularity.
+//
+// One CTA (128 threads, one per tensor-memory lane) per tile of G lines,
+// persistent over tiles.  The B operands (hi / lo images of both passes) are
+// built once per plan in global memory and copied to shared memory when the
+// CTA starts.  Per tile: the lines of the next tile are fetched (cp.async)
+// into the second line buffer while this tile runs; each thread stages one
+// row of A per 128-row block (16-byte stores of whole core-matrix rows, one
+// integer division per row); thread 0 issues the MMAs of a block and commits
+// them to an mbarrier; every thread reads its row of D from tensor memory
+// and writes it back into the line buffer; a coalesced store writes the
+// tile to the next ordering as in the other stage kernels.
+//
+// Line buffer layout: line g at g * np; pass 1 writes Y[t][q] at t * Rp + q
+// with Rp = R rounded up to odd (conflict-free row-per-thread stores), and np
+// (>= S Rp) is an odd multiple of 16 / G so that the store phase, which reads
+// one element of each of G lines per group of G threads, is conflict-free.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "../../include/openfft_gb.h"
+#include "fft_stage.h"
+#include "fft_tile.cuh"
+#include "stage_io.cuh"
+#include "tc.cuh"
+
+namespace ofg {
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kTmemCols = 64;                     // N <= 64 (2 * 32)
+constexpr long long kWaitBudget = 2000000000LL;   // about one second of clock cycles
+
+struct GemmShape {
+    int n, R, S, G, Rp, np;
+    int K1, N1, K2, N2;          // padded real K / N of the two passes
+    int M1, M2;                  // rows (G S, G R) padded to multiples of 128
+    int es;                      // operand bytes (4 tf32, 2 bf16)
+    // shared-memory byte offsets; the B image is [b1 hi | b1 lo | b2 hi | b2 lo]
+    int off_lines0, off_lines1, off_ahi, off_alo, off_b, b_bytes, smem;
+    int b1lo, b2hi, b2lo;        // offsets within the B image
+};
+
+__host__ __device__ int pad_to(int v, int m) { return (v + m - 1) / m * m; }
+
+template <bool TF32>
+__device__ __forceinline__ void put_split(unsigned char* hi, unsigned char* lo, uint32_t off, float x)
+{
+    if (TF32) {
+        const float h = tc::round_tf32(x);
+        *reinterpret_cast<float*>(hi + off) = h;
+        *reinterpret_cast<float*>(lo + off) = tc::round_tf32(x - h);
+    } else {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        *reinterpret_cast<__nv_bfloat16*>(hi + off) = h;
+        *reinterpret_cast<__nv_bfloat16*>(lo + off) = __float2bfloat16_rn(x - __bfloat162float(h));
+    }
+}
+
+// One 16-byte K group of a row of A: CPG complex values (2 for tf32, 4 for
+// bf16), real-ified (re, im, re, im, ...), split into hi and lo.
+template <bool TF32>
+__device__ __forceinline__ void put_group(unsigned char* hi, unsigned char* lo, uint32_t off, const float2* x)
+{
+    if (TF32) {
+        float4 h, l;
+        h.x = tc::round_tf32(x[0].x); l.x = tc::round_tf32(x[0].x - h.x);
+        h.y = tc::round_tf32(x[0].y); l.y = tc::round_tf32(x[0].y - h.y);
+        h.z = tc::round_tf32(x[1].x); l.z = tc::round_tf32(x[1].x - h.z);
+        h.w = tc::round_tf32(x[1].y); l.w = tc::round_tf32(x[1].y - h.w);
+        *reinterpret_cast<float4*>(hi + off) = h;
+        *reinterpret_cast<float4*>(lo + off) = l;
+    } else {
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(x[i].x, x[i].y);
+            const float2 hf = __bfloat1622float2(h);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(x[i].x - hf.x, x[i].y - hf.y);
+            hw[i] = *reinterpret_cast<const uint32_t*>(&h);
+            lw[i] = *reinterpret_cast<const uint32_t*>(&l);
+        }
+        *reinterpret_cast<uint4*>(hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4*>(lo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+}
+
+// B image of the real-ified DFT matrices of sizes R (pass 1) and S (pass 2),
+// each N x K, K-major: W_r^{jq} = W_n^{(jq mod r) (n / r)}.
+template <bool TF32>
+__global__ void dftgemm_image_kernel(const float2* __restrict__ tw, GemmShape sh, unsigned char* __restrict__ out)
+{
+    const int es = sh.es;
+    const int e1 = sh.N1 * sh.K1, total = e1 + sh.N2 * sh.K2;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const bool second = idx >= e1;
+        const int e = second ? idx - e1 : idx;
+        const int K = second ? sh.K2 : sh.K1, r = second ? sh.S : sh.R;
+        const int row = e / K, col = e - row * K;
+        float v = 0.f;
+        const int q = row >> 1, j = col >> 1;
+        if (q < r && j < r) {
+            const float2 w = tw[((j * q) % r) * (sh.n / r)];      // (c, -s)
+            const float c = w.x, s = -w.y;
+            const int rr = row & 1, cc = col & 1;
+            v = rr == 0 ? (cc == 0 ? c : s) : (cc == 0 ? -s : c);
+        }
+        unsigned char* hi = out + (second ? sh.b2hi : 0);
+        unsigned char* lo = out + (second ? sh.b2lo : sh.b1lo);
+        put_split<TF32>(hi, lo, tc::op_offset(row, col, K * es / 16, es), v);
+    }
+}
+
+// Issue D = A_hi B_hi + A_hi B_lo + A_lo B_hi for one 128-row block (thread 0).
+template <bool TF32>
+__device__ __forceinline__ void issue_block(uint32_t d_tmem, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi, uint32_t b_lo,
+                                            int K, int N, int es)
+{
+    const int KT = K * es / 16;
+    const uint32_t id = tc::idesc(TF32 ? tc::kTypeTF32 : tc::kTypeBF16, 128, N);
+    const uint32_t pa[3] = {a_hi, a_hi, a_lo};
+    const uint32_t pb[3] = {b_hi, b_lo, b_hi};
+    uint32_t acc = 0;
+    for (int pr = 0; pr < 3; ++pr)
+        for (int kc = 0; kc < KT / 2; ++kc) {
+            const uint64_t ad = tc::smem_desc(pa[pr] + kc * 256, 128, KT * 128);
+            const uint64_t bd = tc::smem_desc(pb[pr] + kc * 256, 128, KT * 128);
+            tc::mma<TF32>(d_tmem, ad, bd, id, acc);
+            acc = 1;
+        }
+}
+
+// Fetch the G lines of `tile` into buf (line g at g * np); lines past the
+// end of the grouped range are zero.
+__device__ __forceinline__ void load_tile(const StageArgs& p, const GemmShape& sh, int64_t tile, float2* buf)
+{
+    const TileGeom tg = tile_geom(p, tile, sh.G);
+    const char* src = reinterpret_cast<const char*>(p.in);
+    const int n = sh.n;
+    int g = 0, i = threadIdx.x;
+    while (i >= n) { i -= n; ++g; }
+    for (; g < sh.G;) {
+        float2* dst = buf + g * sh.np + i;
+        if (g < tg.valid) cp_async<8>(dst, src + ((tg.line0 + g * tg.lstride) * n + i) * 8);
+        else *dst = make_float2(0.f, 0.f);
+        i += kThreads;
+        while (i >= n) { i -= n; ++g; }
+    }
+    cp_async_commit();
+}
+
+// Stage A of pass PASS for every 128-row block: thread tid builds row
+// blk * 128 + tid.  Pass 0 rows (g, t) hold x[t + S j] (j < R); pass 1 rows
+// (g, k) hold W_n^{jk} Y[j][k] (j < S).
+template <bool TF32, int PASS>
+__device__ __forceinline__ void stage_a(const GemmShape& sh, const float2* lines, unsigned char* a_hi,
+                                        unsigned char* a_lo, const float2* __restrict__ tw, int conj_in)
+{
+    constexpr int CPG = TF32 ? 2 : 4;               // complex values per 16-byte K group
+    const int K = PASS ? sh.K2 : sh.K1;
+    const int KT = K * sh.es / 16;
+    const int rows = PASS ? sh.G * sh.R : sh.G * sh.S;
+    const int Mpad = PASS ? sh.M2 : sh.M1;
+    const int jmax = PASS ? sh.S : sh.R;
+    const int div = PASS ? sh.R : sh.S;
+    const int step = PASS ? sh.Rp : sh.S;
+    const int tid = threadIdx.x;
+    for (int blk = 0; blk < Mpad / 128; ++blk) {
+        const int row = blk * 128 + tid;
+        const uint32_t base = (uint32_t)(blk * 128 * K * sh.es) + (uint32_t)((tid >> 3) * KT) * 128 + (tid & 7) * 16;
+        float2 x[CPG];
+        if (row < rows) {
+            const int g = row / div, r = row - g * div;
+            const float2* src = lines + g * sh.np + r;
+            for (int kk = 0; kk < KT; ++kk) {
+#pragma unroll
+                for (int c = 0; c < CPG; ++c) {
+                    const int j = kk * CPG + c;
+                    float2 v = make_float2(0.f, 0.f);
+                    if (j < jmax) {
+                        v = src[j * step];
+                        if (PASS == 0) {
+                            if (conj_in) v.y = -v.y;
+                        } else {
+                            const float2 w = __ldg(tw + j * r);
+                            v = make_float2(fmaf(v.x, w.x, -v.y * w.y), fmaf(v.x, w.y, v.y * w.x));
+                        }
+                    }
+                    x[c] = v;
+                }
+                put_group<TF32>(a_hi, a_lo, base + kk * 128, x);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < CPG; ++c) x[c] = make_float2(0.f, 0.f);
+            for (int kk = 0; kk < KT; ++kk) put_group<TF32>(a_hi, a_lo, base + kk * 128, x);
+        }
+    }
+}
+
+// MMAs and epilogue of pass PASS, one 128-row block at a time.  Pass 0 writes
+// Y[t][q] to line position t * Rp + q, pass 1 writes Z[k + R q].  Returns
+// false (every thread) when a completion wait ran out.
+template <bool TF32, int PASS>
+__device__ __forceinline__ bool gemm_pass(const GemmShape& sh, float2* lines, const unsigned char* smem,
+                                          uint32_t d_tmem, uint64_t* mbar, uint32_t& phase, int* status,
+                                          int* s_abort)
+{
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int K = PASS ? sh.K2 : sh.K1, N = PASS ? sh.N2 : sh.N1;
+    const int rows = PASS ? sh.G * sh.R : sh.G * sh.S;
+    const int Mpad = PASS ? sh.M2 : sh.M1;
+    const int qmax = PASS ? sh.S : sh.R;
+    const int div = PASS ? sh.R : sh.S;
+    const uint32_t a_hi = tc::smem_u32(smem + sh.off_ahi), a_lo = tc::smem_u32(smem + sh.off_alo);
+    const uint32_t bb = tc::smem_u32(smem + sh.off_b);
+    const uint32_t bh = PASS ? bb + sh.b2hi : bb, bl = bb + (PASS ? sh.b2lo : sh.b1lo);
+    for (int blk = 0; blk < Mpad / 128; ++blk) {
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t ao = (uint32_t)(blk * 128 * K * sh.es);
+            issue_block<TF32>(d_tmem, a_hi + ao, a_lo + ao, bh, bl, K, N, sh.es);
+            tc::commit(mbar);
+        }
+        bool ok = tc::mbar_wait(mbar, phase, kWaitBudget);
+        phase ^= 1;
+        ok = __all_sync(0xffffffffu, ok);             // tcgen05.ld is warp-collective
+        if (!ok) { atomicCAS(status, OPENFFT_OK, OPENFFT_ERR_TIMEOUT); *s_abort = 1; }
+        tc::fence_after_sync();
+        if (ok) {
+            const int row = blk * 128 + tid;
+            const bool live = row < rows;
+            const int g = live ? row / div : 0, r = live ? row - g * div : 0;
+            float2* dst = PASS ? lines + g * sh.np + r : lines + g * sh.np + r * sh.Rp;
+            const int qs = PASS ? sh.R : 1;
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                float v[16];
+                tc::ld16(d_tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+                if (live) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int q = (c0 >> 1) + i;
+                        if (q < qmax) dst[q * qs] = make_float2(v[2 * i], v[2 * i + 1]);
+                    }
+                }
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        if (*s_abort) return false;
+    }
+    return true;
+}
+
+// Write the tile to the next ordering (conjugation and scale of backward
+// transforms at the store).
+__device__ __forceinline__ void store_tile(const StageArgs& p, const GemmShape& sh, int64_t tile, const float2* lines)
+{
+    const TileGeom tg = tile_geom(p, tile, sh.G);
+    char* first = reinterpret_cast<char*>(p.out) + tg.obase * 8;
+    const float sc = (float)p.scale;
+    const int n = sh.n, G = sh.G, tid = threadIdx.x;
+    if (!p.contig_store) {
+        const int g = tid & (G - 1), slot = tid / G;
+        if (g < tg.valid)
+            for (int k = slot; k < n; k += kThreads / G) {
+                float2 v = lines[g * sh.np + k];
+                if (p.conj_out) v = make_float2(v.x * sc, -v.y * sc);
+                *reinterpret_cast<float2*>(first + (g * tg.ostride + (int64_t)k * p.Sk) * 8) = v;
+            }
+    } else {
+        int g = 0, k = tid;
+        while (k >= n) { k -= n; ++g; }
+        while (g < tg.valid) {
+            float2 v = lines[g * sh.np + k];
+            if (p.conj_out) v = make_float2(v.x * sc, -v.y * sc);
+            *reinterpret_cast<float2*>(first + (g * tg.ostride + (int64_t)k * p.Sk) * 8) = v;
+            k += kThreads;
+            while (k >= n) { k -= n; ++g; }
+        }
+    }
+}
+
+template <bool TF32>
+__global__ void __launch_bounds__(kThreads) dftgemm_kernel(const StageArgs p, const GemmShape sh, int64_t ntiles,
+                                                           int* status)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    float2* const buf0 = reinterpret_cast<float2*>(smem + sh.off_lines0);
+    float2* const buf1 = reinterpret_cast<float2*>(smem + sh.off_lines1);
+    unsigned char* a_hi = smem + sh.off_ahi;
+    unsigned char* a_lo = smem + sh.off_alo;
+    const float2* tw = reinterpret_cast<const float2*>(p.tw);
+
+    // B image -> shared memory, first tile -> line buffer 0
+    const char* bsrc = reinterpret_cast<const char*>(p.aux);
+    for (int o = tid * 16; o < sh.b_bytes; o += kThreads * 16) cp_async<16>(smem + sh.off_b + o, bsrc + o);
+    int64_t tile = blockIdx.x;
+    if (tile < ntiles) load_tile(p, sh, tile, buf0);
+    if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
+    if (tid == 0) { tc::mbar_init(&mbar, 1); s_abort = 0; }
+    cp_async_wait_all();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t d_tmem = tmem_base;
+    uint32_t phase = 0;
+    int cur = 0;
+
+    for (; tile < ntiles; tile += gridDim.x) {
+        float2* lines = cur ? buf1 : buf0;
+        if (tile + gridDim.x < ntiles) load_tile(p, sh, tile + gridDim.x, cur ? buf0 : buf1);
+        stage_a<TF32, 0>(sh, lines, a_hi, a_lo, tw, p.conj_in);
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (!gemm_pass<TF32, 0>(sh, lines, smem, d_tmem, &mbar, phase, status, &s_abort)) break;
+        stage_a<TF32, 1>(sh, lines, a_hi, a_lo, tw, 0);
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (!gemm_pass<TF32, 1>(sh, lines, smem, d_tmem, &mbar, phase, status, &s_abort)) break;
+        store_tile(p, sh, tile, lines);
+        cp_async_wait_all();            // the next tile has landed (this thread's copies)
+        __syncthreads();                // ... and everyone's; this buffer is free again
+        cur ^= 1;
+    }
+    cp_async_wait_all();                // no copy left in flight on an early exit
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(d_tmem, kTmemCols);
+}
+
+// Least np >= S * Rp that is an odd multiple of 16 / G (G <= 16), odd for G >= 16.
+int line_stride(int base, int G)
+{
+    const int m = G >= 16 ? 1 : 16 / G;
+    int np = pad_to(base, m);
+    if ((np / m) % 2 == 0) np += m;
+    return np;
+}
+
+GemmShape make_shape(int n, int R, int S, int G, bool tf32)
+{
+    GemmShape g;
+    const int kstep = tf32 ? 8 : 16;
+    g.n = n; g.R = R; g.S = S; g.G = G; g.es = tf32 ? 4 : 2;
+    g.Rp = R | 1;
+    g.np = line_stride(S * g.Rp, G);
+    g.K1 = pad_to(2 * R, kstep); g.N1 = pad_to(2 * R, 16);
+    g.K2 = pad_to(2 * S, kstep); g.N2 = pad_to(2 * S, 16);
+    g.M1 = pad_to(G * S, 128); g.M2 = pad_to(G * R, 128);
+    const int s1 = g.N1 * g.K1 * g.es, s2 = g.N2 * g.K2 * g.es;
+    g.b1lo = s1; g.b2hi = 2 * s1; g.b2lo = 2 * s1 + s2;
+    g.b_bytes = 2 * s1 + 2 * s2;
+    int off = 0;
+    auto take = [&](int bytes) { const int o = off; off += pad_to(bytes, 128); return o; };
+    g.off_lines0 = take(G * g.np * 8);
+    g.off_lines1 = take(G * g.np * 8);
+    const int abytes = std::max(g.M1 * g.K1, g.M2 * g.K2) * g.es;
+    g.off_ahi = take(abytes); g.off_alo = take(abytes);
+    g.off_b = take(g.b_bytes);
+    g.smem = off;
+    return g;
+}
+
+}  // namespace
+
+// Factor n = R S (2 <= R, S <= 32) with the least padded GEMM work.
+bool dftgemm_factor(int n, int tf32, int* R, int* S)
+{
+    const int kstep = tf32 ? 8 : 16;
+    long best = -1;
+    for (int r = 2; r <= 32; ++r) {
+        if (n % r) continue;
+        const int s = n / r;
+        if (s < 2 || s > 32) continue;
+        const long cost = (long)s * pad_to(2 * r, kstep) * pad_to(2 * r, 16) + (long)r * pad_to(2 * s, kstep) * pad_to(2 * s, 16);
+        if (best < 0 || cost < best) { best = cost; *R = r; *S = s; }
+    }
+    return best >= 0;
+}
+
+size_t dftgemm_image_bytes(int n, int R, int S, bool tf32)
+{
+    return (size_t)make_shape(n, R, S, 1, tf32).b_bytes;
+}
+
+cudaError_t launch_dftgemm_image(int n, int R, int S, bool tf32, const void* tw, void* out, cudaStream_t st)
+{
+    const GemmShape sh = make_shape(n, R, S, 1, tf32);
+    const int total = sh.N1 * sh.K1 + sh.N2 * sh.K2;
+    const int blocks = (total + 255) / 256;
+    if (tf32) dftgemm_image_kernel<true><<<blocks, 256, 0, st>>>((const float2*)tw, sh, (unsigned char*)out);
+    else dftgemm_image_kernel<false><<<blocks, 256, 0, st>>>((const float2*)tw, sh, (unsigned char*)out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dftgemm(const StageLaunch& L, cudaStream_t st, int* status)
+{
+    const StageArgs& a = L.args;
+    const bool tf32 = L.arith == ARITH_TC_TF32;
+    const int R = a.radix[0], S = a.radix[1];
+    const GemmShape sh = make_shape(a.n, R, S, a.G, tf32);
+    int per_sm = 1;
+    cudaError_t e;
+    if (tf32) {
+        e = cudaFuncSetAttribute(dftgemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem);
+        if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dftgemm_kernel<true>, kThreads, sh.smem);
+    } else {
+        e = cudaFuncSetAttribute(dftgemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem);
+        if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dftgemm_kernel<false>, kThreads, sh.smem);
+    }
+    if (e) return e;
+    const int max_tmem = 512 / kTmemCols;       // tensor-memory columns per SM
+    if (per_sm > max_tmem) per_sm = max_tmem;
+    const int64_t ntiles = L.grid;
+    int64_t grid = (int64_t)L.sms * (per_sm > 0 ? per_sm : 1);
+    if (grid > ntiles) grid = ntiles;
+    if (grid < 1) grid = 1;
+    if (tf32) dftgemm_kernel<true><<<(unsigned)grid, kThreads, sh.smem, st>>>(a, sh, ntiles, status);
+    else dftgemm_kernel<false><<<(unsigned)grid, kThreads, sh.smem, st>>>(a, sh, ntiles, status);
+    return cudaGetLastError();
+}
+
+// Lines per tile: Gt (a power of two, <= 16) halved until the shared memory fits.
+int dftgemm_lines(int n, int R, int S, bool tf32, int Gt)
+{
+    int G = Gt < 1 ? 1 : (Gt > 16 ? 16 : Gt);
+    while (G > 1 && make_shape(n, R, S, G, tf32).smem > 200 * 1024) G /= 2;
+    return make_shape(n, R, S, G, tf32).smem > 200 * 1024 ? 0 : G;
+}
+
+}  // namespace ofg

@@ -12,8 +12,9 @@ constexpr int kMaxLen = 2048;          // longest supported axis (two tiles of o
 
 // element formats in global memory
 enum { FMT_C128 = 0, FMT_C64 = 1, FMT_DF = 2 };
-// arithmetic
-enum { ARITH_F64 = 0, ARITH_F32 = 1, ARITH_DF = 2 };
+// arithmetic: FP64, FP32, double-float, and the split-precision tensor-core
+// DFT-GEMM forms (complex64 data)
+enum { ARITH_F64 = 0, ARITH_F32 = 1, ARITH_DF = 2, ARITH_TC_TF32 = 3, ARITH_TC_BF16 = 4 };
 
 // Lines of a stage are l = i1 + i2 * M1 (i1 < M1, i2 < M2), each contiguous
 // of length n at in + l * n.  Output element (l, k) goes to
@@ -24,6 +25,7 @@ struct StageArgs {
     const void* in;
     void* out;
     const void* tw;            // twiddle table of length n (W[e] = exp(-2 pi i e / n))
+    const void* aux;           // DFT-GEMM stages: operand image of the DFT matrices
     int64_t M1, M2, S1, S2, Sk;
     int64_t ngroups;           // ceil(M_grouped / G)
     double scale;              // applied at store (1.0 = none)
@@ -42,6 +44,7 @@ struct StageLaunch {
     size_t smem;               // dynamic shared memory of the generic kernel
     int sms;                   // multiprocessors of the device (persistent grids)
     int family;                // KERNEL_*: which stage kernel runs this launch
+    int* status;               // device status word (DFT-GEMM stages)
 };
 
 // stage kernel families: warp-per-line (power-of-two n), tile (specialised n),
@@ -55,5 +58,16 @@ cudaError_t launch_tile_f32(const StageLaunch& L, cudaStream_t st, bool* handled
 cudaError_t launch_tile_df(const StageLaunch& L, cudaStream_t st, bool* handled);
 cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st);
 cudaError_t launch_twiddles(int n, int fmt, void* out, cudaStream_t st);
+
+// DFT-GEMM stages (dftgemm.cu): n = R S with 2 <= R, S <= 32 (radix[0] = R,
+// radix[1] = S); status receives OPENFFT_ERR_TIMEOUT if an MMA wait runs out.
+// The stage reads the split operand image of its two DFT matrices from
+// args.aux (dftgemm_image_bytes bytes, built once by launch_dftgemm_image from
+// the complex64 twiddle table of length n).
+bool dftgemm_factor(int n, int tf32, int* R, int* S);
+int dftgemm_lines(int n, int R, int S, bool tf32, int Gt);
+size_t dftgemm_image_bytes(int n, int R, int S, bool tf32);
+cudaError_t launch_dftgemm_image(int n, int R, int S, bool tf32, const void* tw, void* out, cudaStream_t st);
+cudaError_t launch_dftgemm(const StageLaunch& L, cudaStream_t st, int* status);
 
 }  // namespace ofg

@@ -27,7 +27,7 @@ VARIANT_ISEND_WAITALL, VARIANT_ISEND_WAITALL_BLOCK, VARIANT_ISEND_WAITSOME_BLOCK
 # the paper's methods (Sec. 3.2.1) by name
 METHODS = {"Alltoallv": 0, "Isend_Waitsome": 1, "fused": 2, "Isend_Waitall": 3, "Isend_Waitall_Block": 4,
            "Isend_Waitsome_Block": 5, "Sendrecv": 6}
-ARITH_NATIVE, ARITH_DOUBLE_FLOAT = 0, 1
+ARITH_NATIVE, ARITH_DOUBLE_FLOAT, ARITH_TC_TF32, ARITH_TC_BF16 = 0, 1, 2, 3
 TUNE_DEFAULT, TUNE_EXHAUSTIVE, TUNE_LEARNED, TUNE_USER = 0, 1, 2, 3
 LAYOUT_ABC, LAYOUT_CAB, LAYOUT_CBA = 0, 1, 2
 KERNEL_AUTO, KERNEL_WARP, KERNEL_TILE, KERNEL_GENERIC = 0, 1, 2, 3
