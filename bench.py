@@ -393,6 +393,8 @@ def measure_forms(of, torch, plans_f64, x, y, z, n, stream, args):
         of.openfft_destroy(h5)
         del xb, yb
         torch.cuda.empty_cache()
+        # the learned selector against exhaustive autotuning at 512^3
+        out["learned_vs_exhaustive_512cubed"] = measure_learned(of, torch, stream)
     return out
 
 
@@ -478,6 +480,72 @@ def measure_mixed(of, torch, stream, reps=7):
                      "bound": bound, "chosen": of.openfft_candidate(h, of.openfft_current_candidate(h))}
         of.openfft_destroy(h)
     del flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_learned(of, torch, stream, Ps=(64, 256, 1024), reps=5):
+    """512^3 complex128 (held out of the cost model's training set): the
+    candidate the learned selector proposes against exhaustive autotuning
+    (the paper's run-time choice), both timed by the same protocol; regret =
+    t_learned / t_exhaustive - 1.  Also the host time each way of choosing
+    takes (exhaustive: two timed runs of every candidate; learned: one model
+    evaluation per candidate)."""
+    from paper_1501_07350_gb300 import learned, synth
+    learned.install()
+    n = 512
+    N = n ** 3
+    dev = torch.device("cuda", torch.cuda.current_device())
+    torch.cuda.empty_cache()
+    x = torch.from_numpy(synth.complex_field((N,), seed=synth.config_seed(5))).to(dev)
+    y = torch.empty_like(x)
+
+    def timed(h, ci):
+        of.openfft_set_tuning(h, of.TUNE_USER, ci)
+        for _ in range(2):
+            of.openfft_exec_c2c(h, x, y, of.FORWARD)
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            of.openfft_exec_c2c(h, x, y, of.FORWARD)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    out = {"shape": [n, n, n], "dtype": "complex128", "held_out": True, "per_P": {}}
+    regrets = []
+    for P in Ps:
+        h = of.openfft_plan(n, n, n, P, of.C2C_F64)
+        of.openfft_set_stream(h, stream)
+        t0 = time.perf_counter()
+        of.openfft_set_tuning(h, of.TUNE_EXHAUSTIVE)
+        tune_ex = time.perf_counter() - t0
+        ci_ex = of.openfft_current_candidate(h)
+        t0 = time.perf_counter()
+        of.openfft_set_tuning(h, of.TUNE_LEARNED)
+        tune_l = time.perf_counter() - t0
+        ci_l = of.openfft_current_candidate(h)
+        t_ex, t_l, t_def = timed(h, ci_ex), timed(h, ci_l), timed(h, 0)
+        # the same candidate is the same launch sequence: its regret is 0 and
+        # the two timings differ by measurement noise only
+        same = ci_l == ci_ex
+        regret = 0.0 if same else t_l / t_ex - 1.0
+        regrets.append(regret)
+        out["per_P"][str(P)] = {"exhaustive": {"candidate": of.openfft_candidate(h, ci_ex), "ms": round(t_ex, 3),
+                                               "tuning_s": round(tune_ex, 3)},
+                                "learned": {"candidate": of.openfft_candidate(h, ci_l), "ms": round(t_l, 3),
+                                            "tuning_s": round(tune_l, 4)},
+                                "default_ms": round(t_def, 3), "regret": round(regret, 4), "same_choice": same,
+                                "timing_noise": round(t_l / t_ex - 1.0, 4) if same else None,
+                                "candidates": of.openfft_num_candidates(h)}
+        of.openfft_destroy(h)
+    out["mean_regret"] = round(sum(regrets) / len(regrets), 4)
+    out["max_regret"] = round(max(regrets), 4)
+    out["target"] = "within 5% of exhaustive autotuning"
+    del x, y
     torch.cuda.empty_cache()
     return out
 
@@ -623,8 +691,9 @@ def run_single(args, local_rank):
     pick = None
     for ci in range(of.openfft_num_candidates(h)):
         c = of.openfft_candidate(h, ci)
-        if tc_form and c["arith"] == want_arith and pick is None:
-            pick = ci
+        if tc_form:
+            if c["arith"] == want_arith and c["lines_per_cta"] == args.G:
+                pick = ci
         elif (c["variant"] == want_variant and c["arith"] == want_arith and c["lines_per_cta"] == args.G
                 and (want_variant != of.VARIANT_FUSED
                      or c["kernel"] == {"auto": 0, "warp": 0, "tile": 2, "generic": 3}[args.kernel])):
@@ -662,6 +731,8 @@ def main():
     ap.add_argument("--no-512", dest="no_512", action="store_true", help="skip the 512^3 form")
     ap.add_argument("--no-batch", dest="no_batch", action="store_true", help="skip the batched form")
     ap.add_argument("--only-batch", dest="only_batch", action="store_true", help="time the batched form only")
+    ap.add_argument("--only-learned", dest="only_learned", action="store_true",
+                    help="time the learned selector against exhaustive autotuning at 512^3 only")
     ap.add_argument("--only-mixed", dest="only_mixed", action="store_true",
                     help="time the 120x144x160 FP64 / FP32 / split tensor-core forms only")
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
@@ -692,6 +763,14 @@ def main():
         _build.build()
         torch.cuda.set_device(local_rank)
         print(json.dumps({"batch64": measure_batch(of, torch, torch.cuda.current_stream())}))
+        return
+    if args.only_learned:
+        import torch
+        from paper_1501_07350_gb300 import _build
+        from paper_1501_07350_gb300 import openfft as of
+        _build.build()
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"learned_vs_exhaustive_512cubed": measure_learned(of, torch, torch.cuda.current_stream())}))
         return
     if args.only_mixed:
         import torch

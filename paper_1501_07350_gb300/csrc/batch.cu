@@ -374,9 +374,13 @@ int batch_create(int count, const int* dims, const int* P, int dtype, int sms, B
     int per_sm = 1;
     if (b->arith == ARITH_F32) {
         e = cudaFuncSetAttribute(batch_kernel<ArF32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(b->smem + tables));
+        if (!e) e = cudaFuncSetAttribute(batch_kernel<ArF32, 16>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
         if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<ArF32, 16>, kBatchThreads, b->smem + tables);
     } else {
         e = cudaFuncSetAttribute(batch_kernel<ArDF, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(b->smem + tables));
+        if (!e) e = cudaFuncSetAttribute(batch_kernel<ArDF, 8>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
         if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<ArDF, 8>, kBatchThreads, b->smem + tables);
     }
     if (e) { free_batch(b); return fail(OPENFFT_ERR_CUDA, cudaGetErrorString(e)); }

@@ -13,16 +13,18 @@
 // remainder; D = A_hi B_hi + A_hi B_lo + A_lo B_hi accumulates in fp32 in
 // tensor memory.  K and N are padded with zeros to the MMA granularity.
 //
-// One CTA (128 threads, one per tensor-memory lane) per tile of G lines,
-// persistent over tiles.  The B operands (hi / lo images of both passes) are
-// built once per plan in global memory and copied to shared memory when the
-// CTA starts.  Per tile: the lines of the next tile are fetched (cp.async)
-// into the second line buffer while this tile runs; each thread stages one
-// row of A per 128-row block (16-byte stores of whole core-matrix rows, one
-// integer division per row); thread 0 issues the MMAs of a block and commits
-// them to an mbarrier; every thread reads its row of D from tensor memory
-// and writes it back into the line buffer; a coalesced store writes the
-// tile to the next ordering as in the other stage kernels.
+// One CTA of 256 threads (two warpgroups; warps w and w + 4 share the
+// tensor-memory lanes 32 (w % 4) ..) per tile of G lines, persistent over
+// tiles.  The B operands (hi / lo images of both passes) are built once per
+// plan in global memory and copied, with the twiddle table, to shared memory
+// when the CTA starts.  Per tile and pass: every 128-row block of A is
+// staged (row blk * 128 + lane; warpgroup h takes half of the 16-byte K
+// groups of the row: whole core-matrix rows, one integer division per row),
+// thread 0 issues the MMAs of all blocks (block b accumulates in tensor-memory
+// columns 64 b ..) and commits them to one mbarrier, and every thread reads
+// its share of the 16-column chunks of its row back into the line buffer.
+// The lines of the next tile are loaded into registers while this tile runs
+// and written to shared memory after its store.
 //
 // Line buffer layout: line g at g * np; pass 1 writes Y[t][q] at t * Rp + q
 // with Rp = R rounded up to odd (conflict-free row-per-thread stores), and np
@@ -43,8 +45,9 @@ namespace ofg {
 
 namespace {
 
-constexpr int kThreads = 128;
-constexpr int kTmemCols = 64;                     // N <= 64 (2 * 32)
+constexpr int kThreads = 256;
+constexpr int kPrefetch = 16;                     // register prefetch: up to 16 elements per thread
+constexpr int kMaxBlocks = 4;                     // 128-row blocks per pass (tensor-memory columns 64 each)
 constexpr long long kWaitBudget = 2000000000LL;   // about one second of clock cycles
 
 struct GemmShape {
@@ -52,8 +55,9 @@ struct GemmShape {
     int K1, N1, K2, N2;          // padded real K / N of the two passes
     int M1, M2;                  // rows (G S, G R) padded to multiples of 128
     int es;                      // operand bytes (4 tf32, 2 bf16)
+    int tcols;                   // tensor-memory columns: 64 per 128-row block
     // shared-memory byte offsets; the B image is [b1 hi | b1 lo | b2 hi | b2 lo]
-    int off_lines0, off_lines1, off_ahi, off_alo, off_b, b_bytes, smem;
+    int off_lines, off_ahi, off_alo, off_b, off_tw, b_bytes, smem;
     int b1lo, b2hi, b2lo;        // offsets within the B image
 };
 
@@ -146,126 +150,213 @@ __device__ __forceinline__ void issue_block(uint32_t d_tmem, uint32_t a_hi, uint
         }
 }
 
-// Fetch the G lines of `tile` into buf (line g at g * np); lines past the
-// end of the grouped range are zero.
-__device__ __forceinline__ void load_tile(const StageArgs& p, const GemmShape& sh, int64_t tile, float2* buf)
+// Elements of a tile, walked e = tid + kThreads m: (line g, position i).
+// Global source of line g: in + (line0 + g lstride) n.
+struct TileWalk {
+    const float2* line;          // start of line g in global memory
+    int g, i;
+};
+
+__device__ __forceinline__ void walk_advance(TileWalk& w, const TileGeom& tg, const float2* in, int n)
 {
-    const TileGeom tg = tile_geom(p, tile, sh.G);
-    const char* src = reinterpret_cast<const char*>(p.in);
-    const int n = sh.n;
-    int g = 0, i = threadIdx.x;
-    while (i >= n) { i -= n; ++g; }
-    for (; g < sh.G;) {
-        float2* dst = buf + g * sh.np + i;
-        if (g < tg.valid) cp_async<8>(dst, src + ((tg.line0 + g * tg.lstride) * n + i) * 8);
-        else *dst = make_float2(0.f, 0.f);
-        i += kThreads;
-        while (i >= n) { i -= n; ++g; }
+    w.i += kThreads;
+    if (w.i >= n) {
+        do { w.i -= n; ++w.g; } while (w.i >= n);
+        w.line = in + (tg.line0 + (int64_t)w.g * tg.lstride) * n;
     }
-    cp_async_commit();
 }
 
-// Stage A of pass PASS for every 128-row block: thread tid builds row
-// blk * 128 + tid.  Pass 0 rows (g, t) hold x[t + S j] (j < R); pass 1 rows
-// (g, k) hold W_n^{jk} Y[j][k] (j < S).
+// Load this thread's elements of `tile` into registers (lines past the end
+// of the grouped range read as zero).  cnt = ceil(G n / kThreads) <= kPrefetch.
+__device__ __forceinline__ void fetch_regs(const StageArgs& p, const GemmShape& sh, int64_t tile, float2* r, int cnt)
+{
+    const TileGeom tg = tile_geom(p, tile, sh.G);
+    const float2* in = reinterpret_cast<const float2*>(p.in);
+    TileWalk w;
+    w.g = 0; w.i = threadIdx.x;
+    while (w.i >= sh.n) { w.i -= sh.n; ++w.g; }
+    w.line = in + (tg.line0 + (int64_t)w.g * tg.lstride) * sh.n;
+#pragma unroll
+    for (int m = 0; m < kPrefetch; ++m) {
+        if (m < cnt) {
+            r[m] = (w.g < tg.valid) ? __ldg(w.line + w.i) : make_float2(0.f, 0.f);
+            walk_advance(w, tg, in, sh.n);
+        }
+    }
+}
+
+__device__ __forceinline__ void put_regs(const GemmShape& sh, const float2* r, int cnt, float2* lines)
+{
+    int g = 0, i = threadIdx.x;
+    while (i >= sh.n) { i -= sh.n; ++g; }
+#pragma unroll
+    for (int m = 0; m < kPrefetch; ++m) {
+        if (m < cnt) {
+            if (g < sh.G) lines[g * sh.np + i] = r[m];
+            i += kThreads;
+            while (i >= sh.n) { i -= sh.n; ++g; }
+        }
+    }
+}
+
+// Direct load of a tile (tiles too large for the register prefetch).
+__device__ __forceinline__ void load_tile(const StageArgs& p, const GemmShape& sh, int64_t tile, float2* lines)
+{
+    const TileGeom tg = tile_geom(p, tile, sh.G);
+    const float2* in = reinterpret_cast<const float2*>(p.in);
+    TileWalk w;
+    w.g = 0; w.i = threadIdx.x;
+    while (w.i >= sh.n) { w.i -= sh.n; ++w.g; }
+    w.line = in + (tg.line0 + (int64_t)w.g * tg.lstride) * sh.n;
+    while (w.g < sh.G) {
+        float2* dst = lines + w.g * sh.np + w.i;
+        if (w.g < tg.valid) cp_async<8>(dst, w.line + w.i);
+        else *dst = make_float2(0.f, 0.f);
+        walk_advance(w, tg, in, sh.n);
+    }
+    cp_async_wait_all();
+}
+
+// Stage block blk of A for pass PASS: row blk * 128 + lane, K groups
+// [kk0, kk1) (this warpgroup's half).  Pass 0 rows (g, t) hold x[t + S j]
+// (j < R); pass 1 rows (g, k) hold W_n^{jk} Y[j][k] (j < S).
 template <bool TF32, int PASS>
-__device__ __forceinline__ void stage_a(const GemmShape& sh, const float2* lines, unsigned char* a_hi,
-                                        unsigned char* a_lo, const float2* __restrict__ tw, int conj_in)
+__device__ __forceinline__ void stage_block(const GemmShape& sh, const float2* lines, unsigned char* a_hi,
+                                            unsigned char* a_lo, const float2* tws, int conj_in, int blk)
 {
     constexpr int CPG = TF32 ? 2 : 4;               // complex values per 16-byte K group
     const int K = PASS ? sh.K2 : sh.K1;
     const int KT = K * sh.es / 16;
     const int rows = PASS ? sh.G * sh.R : sh.G * sh.S;
-    const int Mpad = PASS ? sh.M2 : sh.M1;
     const int jmax = PASS ? sh.S : sh.R;
     const int div = PASS ? sh.R : sh.S;
     const int step = PASS ? sh.Rp : sh.S;
-    const int tid = threadIdx.x;
-    for (int blk = 0; blk < Mpad / 128; ++blk) {
-        const int row = blk * 128 + tid;
-        const uint32_t base = (uint32_t)(blk * 128 * K * sh.es) + (uint32_t)((tid >> 3) * KT) * 128 + (tid & 7) * 16;
-        float2 x[CPG];
-        if (row < rows) {
-            const int g = row / div, r = row - g * div;
-            const float2* src = lines + g * sh.np + r;
-            for (int kk = 0; kk < KT; ++kk) {
+    const int lane = threadIdx.x & 127, half = threadIdx.x >> 7;
+    const int kh = (KT + 1) >> 1;
+    const int kk0 = half ? kh : 0, kk1 = half ? KT : kh;
+    const int row = blk * 128 + lane;
+    const uint32_t base = (uint32_t)(blk * 128 * K * sh.es) + (uint32_t)((lane >> 3) * KT) * 128 + (lane & 7) * 16;
+    float2 x[CPG];
+    if (row < rows) {
+        const int g = row / div, r = row - g * div;
+        // groups [kk0, kfull) hold only real entries (j < jmax); [kfull, kk1) the padded tail
+        const int kfull = max(kk0, min(kk1, jmax / CPG));
+        const float2* sp = lines + g * sh.np + r + kk0 * CPG * step;
+        const float2* tp = tws + kk0 * CPG * r;
+        uint32_t off = base + kk0 * 128;
+        for (int kk = kk0; kk < kfull; ++kk, off += 128) {
 #pragma unroll
-                for (int c = 0; c < CPG; ++c) {
-                    const int j = kk * CPG + c;
-                    float2 v = make_float2(0.f, 0.f);
-                    if (j < jmax) {
-                        v = src[j * step];
-                        if (PASS == 0) {
-                            if (conj_in) v.y = -v.y;
-                        } else {
-                            const float2 w = __ldg(tw + j * r);
-                            v = make_float2(fmaf(v.x, w.x, -v.y * w.y), fmaf(v.x, w.y, v.y * w.x));
-                        }
-                    }
-                    x[c] = v;
+            for (int c = 0; c < CPG; ++c) {
+                float2 v = *sp;
+                sp += step;
+                if (PASS == 0) {
+                    if (conj_in) v.y = -v.y;
+                } else {
+                    const float2 w = *tp;
+                    tp += r;
+                    v = make_float2(fmaf(v.x, w.x, -v.y * w.y), fmaf(v.x, w.y, v.y * w.x));
                 }
-                put_group<TF32>(a_hi, a_lo, base + kk * 128, x);
+                x[c] = v;
             }
-        } else {
-#pragma unroll
-            for (int c = 0; c < CPG; ++c) x[c] = make_float2(0.f, 0.f);
-            for (int kk = 0; kk < KT; ++kk) put_group<TF32>(a_hi, a_lo, base + kk * 128, x);
+            put_group<TF32>(a_hi, a_lo, off, x);
         }
+        for (int kk = kfull; kk < kk1; ++kk, off += 128) {
+#pragma unroll
+            for (int c = 0; c < CPG; ++c) {
+                const int j = kk * CPG + c;
+                float2 v = make_float2(0.f, 0.f);
+                if (j < jmax) {
+                    v = *sp;
+                    if (PASS == 0) {
+                        if (conj_in) v.y = -v.y;
+                    } else {
+                        const float2 w = *tp;
+                        v = make_float2(fmaf(v.x, w.x, -v.y * w.y), fmaf(v.x, w.y, v.y * w.x));
+                    }
+                }
+                sp += step;
+                tp += r;
+                x[c] = v;
+            }
+            put_group<TF32>(a_hi, a_lo, off, x);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < CPG; ++c) x[c] = make_float2(0.f, 0.f);
+        for (int kk = kk0; kk < kk1; ++kk) put_group<TF32>(a_hi, a_lo, base + kk * 128, x);
     }
 }
 
-// MMAs and epilogue of pass PASS, one 128-row block at a time.  Pass 0 writes
-// Y[t][q] to line position t * Rp + q, pass 1 writes Z[k + R q].  Returns
-// false (every thread) when a completion wait ran out.
+// One GEMM pass: each 128-row block is staged and its MMAs issued (block b
+// accumulates in tensor-memory columns 64 b .. and completes on mbar[b]) while
+// the next block is staged; then every block's rows are written back: pass 0
+// writes Y[t][q] to line position t * Rp + q, pass 1 writes Z[k + R q].
+// Returns false (every thread) when a completion wait ran out.
 template <bool TF32, int PASS>
-__device__ __forceinline__ bool gemm_pass(const GemmShape& sh, float2* lines, const unsigned char* smem,
-                                          uint32_t d_tmem, uint64_t* mbar, uint32_t& phase, int* status,
-                                          int* s_abort)
+__device__ __forceinline__ bool gemm_pass(const GemmShape& sh, float2* lines, unsigned char* smem, const float2* tws,
+                                          int conj_in, uint32_t d_tmem, uint64_t* mbar, uint32_t& phases,
+                                          int* status, int* s_abort)
 {
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 127, half = tid >> 7;
     const int K = PASS ? sh.K2 : sh.K1, N = PASS ? sh.N2 : sh.N1;
     const int rows = PASS ? sh.G * sh.R : sh.G * sh.S;
-    const int Mpad = PASS ? sh.M2 : sh.M1;
+    const int nblk = (PASS ? sh.M2 : sh.M1) / 128;
     const int qmax = PASS ? sh.S : sh.R;
     const int div = PASS ? sh.R : sh.S;
-    const uint32_t a_hi = tc::smem_u32(smem + sh.off_ahi), a_lo = tc::smem_u32(smem + sh.off_alo);
-    const uint32_t bb = tc::smem_u32(smem + sh.off_b);
-    const uint32_t bh = PASS ? bb + sh.b2hi : bb, bl = bb + (PASS ? sh.b2lo : sh.b1lo);
-    for (int blk = 0; blk < Mpad / 128; ++blk) {
+    unsigned char* a_hi = smem + sh.off_ahi;
+    unsigned char* a_lo = smem + sh.off_alo;
+    for (int blk = 0; blk < nblk; ++blk) {
+        stage_block<TF32, PASS>(sh, lines, a_hi, a_lo, tws, conj_in, blk);
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        __syncthreads();
         if (tid == 0) {
             tc::fence_after_sync();
+            const uint32_t bb = tc::smem_u32(smem + sh.off_b);
+            const uint32_t bh = PASS ? bb + sh.b2hi : bb, bl = bb + (PASS ? sh.b2lo : sh.b1lo);
             const uint32_t ao = (uint32_t)(blk * 128 * K * sh.es);
-            issue_block<TF32>(d_tmem, a_hi + ao, a_lo + ao, bh, bl, K, N, sh.es);
-            tc::commit(mbar);
+            issue_block<TF32>(d_tmem + (uint32_t)(64 * blk), tc::smem_u32(a_hi) + ao, tc::smem_u32(a_lo) + ao,
+                              bh, bl, K, N, sh.es);
+            tc::commit(&mbar[blk]);
         }
-        bool ok = tc::mbar_wait(mbar, phase, kWaitBudget);
-        phase ^= 1;
+    }
+    const int qs = PASS ? sh.R : 1;
+    for (int blk = 0; blk < nblk; ++blk) {
+        bool ok = tc::mbar_wait(&mbar[blk], (phases >> blk) & 1u, kWaitBudget);
+        phases ^= 1u << blk;
         ok = __all_sync(0xffffffffu, ok);             // tcgen05.ld is warp-collective
-        if (!ok) { atomicCAS(status, OPENFFT_OK, OPENFFT_ERR_TIMEOUT); *s_abort = 1; }
+        if (!ok) { atomicCAS(status, OPENFFT_OK, OPENFFT_ERR_TIMEOUT); *s_abort = 1; continue; }
         tc::fence_after_sync();
-        if (ok) {
-            const int row = blk * 128 + tid;
-            const bool live = row < rows;
-            const int g = live ? row / div : 0, r = live ? row - g * div : 0;
-            float2* dst = PASS ? lines + g * sh.np + r : lines + g * sh.np + r * sh.Rp;
-            const int qs = PASS ? sh.R : 1;
-            for (int c0 = 0; c0 < N; c0 += 16) {
-                float v[16];
-                tc::ld16(d_tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-                if (live) {
+        const int row = blk * 128 + lane;
+        const bool live = row < rows;
+        const int g = live ? row / div : 0, r = live ? row - g * div : 0;
+        float2* dst = PASS ? lines + g * sh.np + r : lines + g * sh.np + r * sh.Rp;
+        const uint32_t taddr = d_tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(64 * blk);
+        // this warpgroup's 16-column chunks: 16 half + 32 i (at most two, N <= 64)
+        const int c0 = 16 * half;
+        if (c0 >= N) continue;
+        float v[32];
+        const bool two = c0 + 32 < N;
+        if (two) tc::ld16x2(taddr + (uint32_t)c0, taddr + (uint32_t)(c0 + 32), v);
+        else tc::ld16(taddr + (uint32_t)c0, v);
+        if (live) {
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int q = (c0 >> 1) + i;
-                        if (q < qmax) dst[q * qs] = make_float2(v[2 * i], v[2 * i + 1]);
-                    }
+            for (int i = 0; i < 8; ++i) {
+                const int q = (c0 >> 1) + i;
+                if (q < qmax) dst[q * qs] = make_float2(v[2 * i], v[2 * i + 1]);
+            }
+            if (two) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int q = ((c0 + 32) >> 1) + i;
+                    if (q < qmax) dst[q * qs] = make_float2(v[16 + 2 * i], v[16 + 2 * i + 1]);
                 }
             }
         }
-        tc::fence_before_sync();
-        __syncthreads();
-        if (*s_abort) return false;
     }
-    return true;
+    tc::fence_before_sync();
+    __syncthreads();
+    return *s_abort == 0;
 }
 
 // Write the tile to the next ordering (conjugation and scale of backward
@@ -273,24 +364,27 @@ __device__ __forceinline__ bool gemm_pass(const GemmShape& sh, float2* lines, co
 __device__ __forceinline__ void store_tile(const StageArgs& p, const GemmShape& sh, int64_t tile, const float2* lines)
 {
     const TileGeom tg = tile_geom(p, tile, sh.G);
-    char* first = reinterpret_cast<char*>(p.out) + tg.obase * 8;
+    float2* first = reinterpret_cast<float2*>(p.out) + tg.obase;
     const float sc = (float)p.scale;
     const int n = sh.n, G = sh.G, tid = threadIdx.x;
     if (!p.contig_store) {
-        const int g = tid & (G - 1), slot = tid / G;
-        if (g < tg.valid)
-            for (int k = slot; k < n; k += kThreads / G) {
+        const int g = tid & (G - 1), slot = tid / G, kstep = kThreads / G;
+        if (g < tg.valid) {
+            float2* o = first + g * tg.ostride + (int64_t)slot * p.Sk;
+            const int64_t ostep = (int64_t)kstep * p.Sk;
+            for (int k = slot; k < n; k += kstep, o += ostep) {
                 float2 v = lines[g * sh.np + k];
                 if (p.conj_out) v = make_float2(v.x * sc, -v.y * sc);
-                *reinterpret_cast<float2*>(first + (g * tg.ostride + (int64_t)k * p.Sk) * 8) = v;
+                *o = v;
             }
+        }
     } else {
         int g = 0, k = tid;
         while (k >= n) { k -= n; ++g; }
         while (g < tg.valid) {
             float2 v = lines[g * sh.np + k];
             if (p.conj_out) v = make_float2(v.x * sc, -v.y * sc);
-            *reinterpret_cast<float2*>(first + (g * tg.ostride + (int64_t)k * p.Sk) * 8) = v;
+            first[g * tg.ostride + (int64_t)k * p.Sk] = v;
             k += kThreads;
             while (k >= n) { k -= n; ++g; }
         }
@@ -302,55 +396,58 @@ __global__ void __launch_bounds__(kThreads) dftgemm_kernel(const StageArgs p, co
                                                            int* status)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar[kMaxBlocks];
     __shared__ uint32_t tmem_base;
     __shared__ int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5;
-    float2* const buf0 = reinterpret_cast<float2*>(smem + sh.off_lines0);
-    float2* const buf1 = reinterpret_cast<float2*>(smem + sh.off_lines1);
-    unsigned char* a_hi = smem + sh.off_ahi;
-    unsigned char* a_lo = smem + sh.off_alo;
-    const float2* tw = reinterpret_cast<const float2*>(p.tw);
+    float2* const lines = reinterpret_cast<float2*>(smem + sh.off_lines);
+    float2* const tws = reinterpret_cast<float2*>(smem + sh.off_tw);
+    const int cnt = (sh.G * sh.n + kThreads - 1) / kThreads;
+    const bool prefetch = cnt <= kPrefetch;
 
-    // B image -> shared memory, first tile -> line buffer 0
+    // B image and twiddle table -> shared memory
     const char* bsrc = reinterpret_cast<const char*>(p.aux);
     for (int o = tid * 16; o < sh.b_bytes; o += kThreads * 16) cp_async<16>(smem + sh.off_b + o, bsrc + o);
-    int64_t tile = blockIdx.x;
-    if (tile < ntiles) load_tile(p, sh, tile, buf0);
-    if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
-    if (tid == 0) { tc::mbar_init(&mbar, 1); s_abort = 0; }
+    const float2* twg = reinterpret_cast<const float2*>(p.tw);
+    for (int i = tid; i < sh.n; i += kThreads) tws[i] = twg[i];
+    if (warp == 0) tc::tmem_alloc(&tmem_base, (uint32_t)sh.tcols);
+    if (tid == 0) {
+        for (int b = 0; b < kMaxBlocks; ++b) tc::mbar_init(&mbar[b], 1);
+        s_abort = 0;
+    }
     cp_async_wait_all();
+    int64_t tile = blockIdx.x;
+    float2 r[kPrefetch];
+    if (tile < ntiles && prefetch) {
+        fetch_regs(p, sh, tile, r, cnt);
+        put_regs(sh, r, cnt, lines);
+    }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t d_tmem = tmem_base;
-    uint32_t phase = 0;
-    int cur = 0;
+    uint32_t phases = 0;                              // bit b: phase of mbar[b]
 
     for (; tile < ntiles; tile += gridDim.x) {
-        float2* lines = cur ? buf1 : buf0;
-        if (tile + gridDim.x < ntiles) load_tile(p, sh, tile + gridDim.x, cur ? buf0 : buf1);
-        stage_a<TF32, 0>(sh, lines, a_hi, a_lo, tw, p.conj_in);
-        tc::fence_smem_to_async();
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        if (!gemm_pass<TF32, 0>(sh, lines, smem, d_tmem, &mbar, phase, status, &s_abort)) break;
-        stage_a<TF32, 1>(sh, lines, a_hi, a_lo, tw, 0);
-        tc::fence_smem_to_async();
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        if (!gemm_pass<TF32, 1>(sh, lines, smem, d_tmem, &mbar, phase, status, &s_abort)) break;
+        const int64_t next = tile + gridDim.x;
+        if (!prefetch) {
+            load_tile(p, sh, tile, lines);
+            __syncthreads();
+        } else if (next < ntiles) {
+            fetch_regs(p, sh, next, r, cnt);          // in flight while this tile runs
+        }
+        if (!gemm_pass<TF32, 0>(sh, lines, smem, tws, p.conj_in, d_tmem, mbar, phases, status, &s_abort)) break;
+        if (!gemm_pass<TF32, 1>(sh, lines, smem, tws, 0, d_tmem, mbar, phases, status, &s_abort)) break;
         store_tile(p, sh, tile, lines);
-        cp_async_wait_all();            // the next tile has landed (this thread's copies)
-        __syncthreads();                // ... and everyone's; this buffer is free again
-        cur ^= 1;
+        __syncthreads();                              // every read of this tile's lines is done
+        if (prefetch && next < ntiles) {
+            put_regs(sh, r, cnt, lines);
+            __syncthreads();
+        }
     }
-    cp_async_wait_all();                // no copy left in flight on an early exit
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(d_tmem, kTmemCols);
+    if (warp == 0) tc::tmem_dealloc(d_tmem, (uint32_t)sh.tcols);
 }
 
 // Least np >= S * Rp that is an odd multiple of 16 / G (G <= 16), odd for G >= 16.
@@ -372,16 +469,18 @@ GemmShape make_shape(int n, int R, int S, int G, bool tf32)
     g.K1 = pad_to(2 * R, kstep); g.N1 = pad_to(2 * R, 16);
     g.K2 = pad_to(2 * S, kstep); g.N2 = pad_to(2 * S, 16);
     g.M1 = pad_to(G * S, 128); g.M2 = pad_to(G * R, 128);
+    const int nblk = std::max(g.M1, g.M2) / 128;
+    g.tcols = nblk <= 1 ? 64 : (nblk <= 2 ? 128 : (nblk <= 4 ? 256 : 512));
     const int s1 = g.N1 * g.K1 * g.es, s2 = g.N2 * g.K2 * g.es;
     g.b1lo = s1; g.b2hi = 2 * s1; g.b2lo = 2 * s1 + s2;
     g.b_bytes = 2 * s1 + 2 * s2;
     int off = 0;
     auto take = [&](int bytes) { const int o = off; off += pad_to(bytes, 128); return o; };
-    g.off_lines0 = take(G * g.np * 8);
-    g.off_lines1 = take(G * g.np * 8);
+    g.off_lines = take(G * g.np * 8);
     const int abytes = std::max(g.M1 * g.K1, g.M2 * g.K2) * g.es;
     g.off_ahi = take(abytes); g.off_alo = take(abytes);
     g.off_b = take(g.b_bytes);
+    g.off_tw = take(n * 8);
     g.smem = off;
     return g;
 }
@@ -424,20 +523,35 @@ cudaError_t launch_dftgemm(const StageLaunch& L, cudaStream_t st, int* status)
     const bool tf32 = L.arith == ARITH_TC_TF32;
     const int R = a.radix[0], S = a.radix[1];
     const GemmShape sh = make_shape(a.n, R, S, a.G, tf32);
-    int per_sm = 1;
     cudaError_t e;
+    cudaFuncAttributes fa;
     if (tf32) {
         e = cudaFuncSetAttribute(dftgemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem);
-        if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dftgemm_kernel<true>, kThreads, sh.smem);
+        if (!e) e = cudaFuncSetAttribute(dftgemm_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+        if (!e) e = cudaFuncGetAttributes(&fa, dftgemm_kernel<true>);
     } else {
         e = cudaFuncSetAttribute(dftgemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem);
-        if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dftgemm_kernel<false>, kThreads, sh.smem);
+        if (!e) e = cudaFuncSetAttribute(dftgemm_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+        if (!e) e = cudaFuncGetAttributes(&fa, dftgemm_kernel<false>);
     }
     if (e) return e;
-    const int max_tmem = 512 / kTmemCols;       // tensor-memory columns per SM
-    if (per_sm > max_tmem) per_sm = max_tmem;
+    // resident CTAs per SM from the kernel's own limits: shared memory,
+    // registers, threads and tensor-memory columns (512 per SM; a CTA that
+    // cannot allocate would wait for another to finish)
+    int dev = 0, smem_sm = 0, resv = 0, regs_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    const int cta_smem = sh.smem + (int)fa.sharedSizeBytes + resv;
+    const int cta_regs = ((fa.numRegs + 7) & ~7) * kThreads;
+    int per_sm = std::min({smem_sm / std::max(1, cta_smem), regs_sm / std::max(1, cta_regs), 2048 / kThreads,
+                           512 / sh.tcols});
+    if (per_sm < 1) per_sm = 1;
     const int64_t ntiles = L.grid;
-    int64_t grid = (int64_t)L.sms * (per_sm > 0 ? per_sm : 1);
+    int64_t grid = (int64_t)L.sms * per_sm;
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
     if (tf32) dftgemm_kernel<true><<<(unsigned)grid, kThreads, sh.smem, st>>>(a, sh, ntiles, status);
@@ -448,9 +562,13 @@ cudaError_t launch_dftgemm(const StageLaunch& L, cudaStream_t st, int* status)
 // Lines per tile: Gt (a power of two, <= 16) halved until the shared memory fits.
 int dftgemm_lines(int n, int R, int S, bool tf32, int Gt)
 {
+    auto fits = [&](int G) {
+        const GemmShape sh = make_shape(n, R, S, G, tf32);
+        return sh.smem <= 200 * 1024 && sh.tcols <= 256;
+    };
     int G = Gt < 1 ? 1 : (Gt > 16 ? 16 : Gt);
-    while (G > 1 && make_shape(n, R, S, G, tf32).smem > 200 * 1024) G /= 2;
-    return make_shape(n, R, S, G, tf32).smem > 200 * 1024 ? 0 : G;
+    while (G > 1 && !fits(G)) G /= 2;
+    return fits(G) ? G : 0;
 }
 
 }  // namespace ofg
