@@ -320,13 +320,21 @@ __device__ __forceinline__ bool gemm_pass(const GemmShape& sh, float2* lines, un
             tc::commit(&mbar[blk]);
         }
     }
+    // Completion: the commit after the last block tracks every MMA of the
+    // pass.  Warp 0 polls it; the other warps wait at the barrier, where they
+    // take no issue slots from the other CTAs on the SM.
+    const int last = nblk - 1;
+    if (warp == 0) {
+        bool ok = tc::mbar_wait(&mbar[last], (phases >> last) & 1u, kWaitBudget);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok && tid == 0) { atomicCAS(status, OPENFFT_OK, OPENFFT_ERR_TIMEOUT); *s_abort = 1; }
+    }
+    phases ^= (1u << nblk) - 1u;                      // every block's barrier completed one phase
+    __syncthreads();
+    if (*s_abort) return false;
+    tc::fence_after_sync();
     const int qs = PASS ? sh.R : 1;
     for (int blk = 0; blk < nblk; ++blk) {
-        bool ok = tc::mbar_wait(&mbar[blk], (phases >> blk) & 1u, kWaitBudget);
-        phases ^= 1u << blk;
-        ok = __all_sync(0xffffffffu, ok);             // tcgen05.ld is warp-collective
-        if (!ok) { atomicCAS(status, OPENFFT_OK, OPENFFT_ERR_TIMEOUT); *s_abort = 1; continue; }
-        tc::fence_after_sync();
         const int row = blk * 128 + lane;
         const bool live = row < rows;
         const int g = live ? row / div : 0, r = live ? row - g * div : 0;

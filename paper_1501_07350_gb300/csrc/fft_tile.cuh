@@ -122,7 +122,17 @@ struct TileGeom {
 __device__ __forceinline__ TileGeom tile_geom(const StageArgs& p, int64_t tile, int G)
 {
     TileGeom t;
-    const int64_t outer = tile / p.ngroups, grp = tile - outer * p.ngroups;
+    // 32-bit division whenever the operands fit (launch grids always do):
+    // the 64-bit one is a long software sequence run twice per tile
+    int64_t outer, grp;
+    if (((uint64_t)tile | (uint64_t)p.ngroups) >> 32 == 0) {
+        const uint32_t o = (uint32_t)tile / (uint32_t)p.ngroups;
+        outer = o;
+        grp = (int64_t)((uint32_t)tile - o * (uint32_t)p.ngroups);
+    } else {
+        outer = tile / p.ngroups;
+        grp = tile - outer * p.ngroups;
+    }
     const int64_t first = grp * G;
     if (!p.group_i2) {
         t.line0 = first + outer * p.M1; t.lstride = 1;

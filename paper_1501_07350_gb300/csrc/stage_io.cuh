@@ -76,40 +76,28 @@ __device__ __forceinline__ float2 split_f64(double d)
     return make_float2(h, r);
 }
 
-// (h, l) -> double of h + l, truncated toward the float significand of the
-// renormalised hi part: TwoSum gives s + e = h + l with |e| <= ulp(s)/2; the
-// double takes s's sign, exponent and 24-bit significand and adds e, scaled
-// to the double's last place, into the low 29 bits (a 64-bit add on two
-// 32-bit words).  A borrow below 2^52 (s a power of two, e < 0) lowers the
-// exponent by one.
+// Exact float -> double by bit manipulation (no conversion unit): the sign
+// stays, the exponent is rebiased (+896) and the 23 fraction bits become the
+// top of the 52.  Zero and subnormal floats give a signed zero (a subnormal
+// lo part is below 2^-126, far under the hi part's last place); infinities and
+// NaNs keep their class.
+__device__ __forceinline__ double f2d_bits(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t sign = b & 0x80000000u;
+    const uint32_t e = (b >> 23) & 0xFFu;
+    uint32_t hw = sign | (((b >> 3) & 0x0FFFFFFFu) + (896u << 20));
+    uint32_t lw = b << 29;
+    if (e == 0) { hw = sign; lw = 0; }
+    else if (e == 255) { hw = sign | 0x7FF00000u | ((b & 0x7FFFFFu) ? 0x80000u : 0u); lw = 0; }
+    return __hiloint2double((int)hw, (int)lw);
+}
+
+// (h, l) -> the double nearest h + l: both parts are exact as doubles, and one
+// FP64 addition (on the otherwise idle FP64 pipe) rounds their sum once.
 __device__ __forceinline__ double join_f64(float h, float l)
 {
-    float s, e;
-    ArDF::two_sum(h, l, s, e);
-    const uint32_t sb = __float_as_uint(s);
-    const uint32_t sign = sb & 0x80000000u;
-    const int es = (int)((sb >> 23) & 0xFFu);
-    if (es == 0 || es == 255) {                    // zero / tiny, inf / nan
-        const uint32_t hw = sign | (es == 255 ? (0x7FF00000u | ((sb & 0x7FFFFFu) ? 0x80000u : 0u)) : 0u);
-        return __hiloint2double((int)hw, 0);
-    }
-    const uint32_t man = sb & 0x7FFFFFu;
-    const uint32_t eb = __float_as_uint(e);
-    const int ee = (int)((eb >> 23) & 0xFFu);
-    int32_t d = 0;                                  // e in units of 2^(es-127-52), |d| < 2^29
-    if (ee != 0) {
-        const int32_t me = (int32_t)((1u << 23) | (eb & 0x7FFFFFu));
-        const int sh = ee - es + 29;
-        d = sh >= 0 ? (me << sh) : (sh > -31 ? (me >> -sh) : 0);
-        if ((eb ^ sb) & 0x80000000u) d = -d;
-    }
-    // significand (1 << 52 | man << 29) + d as (hi21:lo32)
-    unsigned long long M = ((unsigned long long)((1u << 20) | (man >> 3)) << 32) | (man << 29);
-    M += (unsigned long long)(long long)d;
-    int E = es + 896;                               // es - 127 + 1023
-    if (!(M >> 52)) { M <<= 1; E -= 1; }
-    const uint32_t hw = sign | ((uint32_t)E << 20) | ((uint32_t)(M >> 32) & 0xFFFFFu);
-    return __hiloint2double((int)hw, (int)(uint32_t)M);
+    return __dadd_rn(f2d_bits(h), f2d_bits(l));
 }
 
 __device__ __forceinline__ float4 df_from_double2(double2 v) {
