@@ -72,23 +72,31 @@ def stage_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel_hash: str):
-    """DRAM bytes per stage launch from the committed ncu summary of the dominant
-    kernel, if it was taken on the current kernel sources."""
-    path = os.path.join(ROOT, "profiles", "fft_warp_kernel_df_256cubed.md")
+def profiled_traffic(kernel_hash: str, family: str, G: int):
+    """DRAM bytes per stage launch of the double-float stage kernel of `family`
+    with G lines per CTA, from the committed ncu summary, if it was taken on
+    the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "fft_%s_kernel_df_256cubed.md" % family)
     vals = {}
     try:
         with open(path) as fh:
             for line in fh:
                 line = line.strip()
-                for key in ("source_hash:", "dram_bytes_per_launch:"):
+                for key in ("source_hash:", "dram_bytes_per_launch G%d:" % G):
                     if line.startswith(key):
                         vals[key[:-1]] = line[len(key):].strip()
         if vals.get("source_hash") == kernel_hash:
-            return float(vals["dram_bytes_per_launch"])
+            return float(vals["dram_bytes_per_launch G%d" % G])
     except Exception:
         pass
     return None
+
+
+def dominant_kernel(chosen: dict):
+    """(family, G) that most of the timed plans use (ties: the first P)."""
+    fam = {0: "warp", 1: "warp", 2: "tile", 3: "generic"}
+    picks = [(fam[c["kernel"]], c["lines_per_cta"]) for c in chosen.values()]
+    return max(picks, key=picks.count)
 
 
 class ClockSampler:
@@ -255,10 +263,14 @@ def run_ours(args, rank, world, local_rank):
     alg_bytes = 2 * N * 16                     # one read + one write of the array per stage launch
     achieved = alg_bytes / avg_s / 1e9
     khash = stage_source_hash()
-    traffic = profiled_traffic(khash)
+    family, G_dom = dominant_kernel(chosen)
+    traffic = profiled_traffic(khash, family, G_dom)
+    arith_name = "ArDF" if all(c["arith"] == of.ARITH_DOUBLE_FLOAT for c in chosen.values()) else "ArF64"
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": "FFT stage kernel (chosen family)", "peak_kind": peak_kind,
+                "kernel": "fft_%s_kernel<%s, %d, G=%d> (the tuned stage kernel of most plans; every stage "
+                          "launch of the step is one of the chosen stage kernels)" % (family, arith_name, n, G_dom),
+                "peak_kind": peak_kind,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_us": round(avg_s * 1e6, 2),
                 "share_of_step": round(fft_ms / max(1e-9, phases["exec"]["ms"]), 4)}
 

@@ -567,7 +567,9 @@ cudaError_t launch_dftgemm(const StageLaunch& L, cudaStream_t st, int* status)
     return cudaGetLastError();
 }
 
-// Lines per tile: Gt (a power of two, <= 16) halved until the shared memory fits.
+// Lines per tile: Gt (a power of two, <= 16) halved until the shared memory
+// fits, and while it is above 4 until two CTAs fit on an SM (a single CTA per
+// SM leaves the MMA and barrier latencies of a tile exposed).
 int dftgemm_lines(int n, int R, int S, bool tf32, int Gt)
 {
     auto fits = [&](int G) {
@@ -576,6 +578,7 @@ int dftgemm_lines(int n, int R, int S, bool tf32, int Gt)
     };
     int G = Gt < 1 ? 1 : (Gt > 16 ? 16 : Gt);
     while (G > 1 && !fits(G)) G /= 2;
+    while (G > 4 && make_shape(n, R, S, G, tf32).smem > 112 * 1024) G /= 2;
     return fits(G) ? G : 0;
 }
 
