@@ -372,17 +372,10 @@ int batch_create(int count, const int* dims, const int* P, int dtype, int sms, B
     const size_t tables = sizeof(int64_t) * (size_t)(3 * count + 1) + sizeof(unsigned) * (size_t)(3 * count);
     if (b->smem + tables > 200 * 1024) { free_batch(b); return fail(OPENFFT_ERR_UNSUPPORTED, "batch too large for the queue tables in shared memory"); }
     int per_sm = 1;
-    if (b->arith == ARITH_F32) {
-        e = cudaFuncSetAttribute(batch_kernel<ArF32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(b->smem + tables));
-        if (!e) e = cudaFuncSetAttribute(batch_kernel<ArF32, 16>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                         (int)cudaSharedmemCarveoutMaxShared);
-        if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<ArF32, 16>, kBatchThreads, b->smem + tables);
-    } else {
-        e = cudaFuncSetAttribute(batch_kernel<ArDF, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(b->smem + tables));
-        if (!e) e = cudaFuncSetAttribute(batch_kernel<ArDF, 8>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                         (int)cudaSharedmemCarveoutMaxShared);
-        if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<ArDF, 8>, kBatchThreads, b->smem + tables);
-    }
+    if (b->arith == ARITH_F32)
+        e = persistent_ctas_per_sm((const void*)batch_kernel<ArF32, 16>, kBatchThreads, b->smem + tables, &per_sm);
+    else
+        e = persistent_ctas_per_sm((const void*)batch_kernel<ArDF, 8>, kBatchThreads, b->smem + tables, &per_sm);
     if (e) { free_batch(b); return fail(OPENFFT_ERR_CUDA, cudaGetErrorString(e)); }
     b->grid = sms * (per_sm > 0 ? per_sm : 1);
     e = cudaDeviceSynchronize();

@@ -531,33 +531,13 @@ cudaError_t launch_dftgemm(const StageLaunch& L, cudaStream_t st, int* status)
     const bool tf32 = L.arith == ARITH_TC_TF32;
     const int R = a.radix[0], S = a.radix[1];
     const GemmShape sh = make_shape(a.n, R, S, a.G, tf32);
-    cudaError_t e;
-    cudaFuncAttributes fa;
-    if (tf32) {
-        e = cudaFuncSetAttribute(dftgemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem);
-        if (!e) e = cudaFuncSetAttribute(dftgemm_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                         (int)cudaSharedmemCarveoutMaxShared);
-        if (!e) e = cudaFuncGetAttributes(&fa, dftgemm_kernel<true>);
-    } else {
-        e = cudaFuncSetAttribute(dftgemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem);
-        if (!e) e = cudaFuncSetAttribute(dftgemm_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                         (int)cudaSharedmemCarveoutMaxShared);
-        if (!e) e = cudaFuncGetAttributes(&fa, dftgemm_kernel<false>);
-    }
+    // resident CTAs: the kernel's own limits, and 512 tensor-memory columns per
+    // SM (a CTA that cannot allocate would wait for another to finish)
+    int per_sm = 1;
+    cudaError_t e = tf32 ? persistent_ctas_per_sm((const void*)dftgemm_kernel<true>, kThreads, sh.smem, &per_sm)
+                         : persistent_ctas_per_sm((const void*)dftgemm_kernel<false>, kThreads, sh.smem, &per_sm);
     if (e) return e;
-    // resident CTAs per SM from the kernel's own limits: shared memory,
-    // registers, threads and tensor-memory columns (512 per SM; a CTA that
-    // cannot allocate would wait for another to finish)
-    int dev = 0, smem_sm = 0, resv = 0, regs_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-    const int cta_smem = sh.smem + (int)fa.sharedSizeBytes + resv;
-    const int cta_regs = ((fa.numRegs + 7) & ~7) * kThreads;
-    int per_sm = std::min({smem_sm / std::max(1, cta_smem), regs_sm / std::max(1, cta_regs), 2048 / kThreads,
-                           512 / sh.tcols});
-    if (per_sm < 1) per_sm = 1;
+    per_sm = std::max(1, std::min(per_sm, 512 / sh.tcols));
     const int64_t ntiles = L.grid;
     int64_t grid = (int64_t)L.sms * per_sm;
     if (grid > ntiles) grid = ntiles;

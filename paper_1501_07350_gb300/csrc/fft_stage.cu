@@ -25,6 +25,8 @@
 #include <type_traits>
 
 #include "fft_stage.h"
+
+#include <algorithm>
 #include "arith.cuh"
 #include "stage_io.cuh"
 #include "generic_stage.cuh"
@@ -63,6 +65,39 @@ __global__ void twiddle_kernel(int n, int fmt, void* out)
 }
 
 // --------------------------------------------------------- host side ----
+
+cudaError_t persistent_ctas_per_sm(const void* func, int threads, size_t dyn_smem, int* per_sm)
+{
+    // cudaOccupancyMaxActiveBlocksPerMultiprocessor has been seen to count one
+    // CTA per SM where two were resident, so the limits are applied here; the
+    // carveout is then set to what those CTAs need, leaving the rest as L1
+    // (which the twiddle loads use)
+    cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+    cudaFuncAttributes fa;
+    if (!e) e = cudaFuncGetAttributes(&fa, func);
+    if (e) return e;
+    int dev = 0, smem_sm = 0, resv = 0, regs_sm = 0, thr_sm = 0, blk_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
+    const long cta_smem = (long)dyn_smem + (long)fa.sharedSizeBytes + resv;
+    const long warps = (threads + 31) / 32;
+    const long cta_regs = (long)((fa.numRegs + 7) & ~7) * 32 * warps;
+    long n = blk_sm > 0 ? blk_sm : 32;
+    if (cta_smem > 0 && smem_sm > 0) n = std::min(n, (long)smem_sm / cta_smem);
+    if (cta_regs > 0) n = std::min(n, (long)regs_sm / cta_regs);
+    n = std::min(n, (long)thr_sm / (32 * warps));
+    if (n < 1) n = 1;
+    *per_sm = (int)n;
+    if (smem_sm > 0) {
+        const long pct = std::min(100L, (100 * n * cta_smem + smem_sm - 1) / smem_sm + 2);
+        e = cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout, (int)pct);
+    }
+    return e;
+}
 
 cudaError_t stage_kernels_init(int max_dyn_smem)
 {

@@ -52,6 +52,11 @@ struct StageLaunch {
 enum { KERNEL_AUTO = 0, KERNEL_WARP = 1, KERNEL_TILE = 2, KERNEL_GENERIC = 3 };
 
 cudaError_t stage_kernels_init(int max_dyn_smem);
+// Resident CTAs per SM of a persistent kernel with `threads` threads and
+// `dyn_smem` bytes of dynamic shared memory, from the kernel's own limits
+// (shared memory with the whole carveout as shared memory, registers,
+// threads); sets the kernel's dynamic shared memory limit and carveout.
+cudaError_t persistent_ctas_per_sm(const void* func, int threads, size_t dyn_smem, int* per_sm);
 // specialised kernels (fft_tile_*.cu); *handled = false when (n, G) has none
 cudaError_t launch_tile_f64(const StageLaunch& L, cudaStream_t st, bool* handled);
 cudaError_t launch_tile_f32(const StageLaunch& L, cudaStream_t st, bool* handled);

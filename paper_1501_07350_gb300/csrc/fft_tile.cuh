@@ -312,13 +312,10 @@ cudaError_t launch_tile_n(const StageLaunch& L, cudaStream_t st)
     const size_t smem = 2 * (size_t)TL::kElems * sizeof(typename A::C);
     static int blocks_per_sm = -1;
     if (blocks_per_sm < 0) {
-        cudaError_t e = cudaFuncSetAttribute(fft_tile_kernel<A, N, G, T>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e) return e;
         int b = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fft_tile_kernel<A, N, G, T>, T, smem);
+        cudaError_t e = persistent_ctas_per_sm((const void*)fft_tile_kernel<A, N, G, T>, T, smem, &b);
         if (e) return e;
-        blocks_per_sm = b > 0 ? b : 1;
+        blocks_per_sm = b;
     }
     const int64_t ntiles = L.grid;
     int64_t grid = (int64_t)L.sms * blocks_per_sm;

@@ -239,13 +239,10 @@ cudaError_t launch_warp_n(const StageLaunch& L, cudaStream_t st)
     const size_t smem = 2 * (size_t)G * warp_line_stride<sizeof(typename A::C)>(N) * sizeof(typename A::C);
     static int blocks_per_sm = -1;
     if (blocks_per_sm < 0) {
-        cudaError_t e = cudaFuncSetAttribute(fft_warp_kernel<A, N, G>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e) return e;
         int b = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fft_warp_kernel<A, N, G>, T, smem);
+        cudaError_t e = persistent_ctas_per_sm((const void*)fft_warp_kernel<A, N, G>, T, smem, &b);
         if (e) return e;
-        blocks_per_sm = b > 0 ? b : 1;
+        blocks_per_sm = b;
     }
     const int64_t ntiles = L.grid;
     int64_t grid = (int64_t)L.sms * blocks_per_sm;
