@@ -199,34 +199,43 @@ __device__ __forceinline__ void warp_store_dispatch(const StageArgs& p, const Ti
 // register budget: 128 per thread for 16-byte elements, 64-80 for 8-byte ones
 constexpr int warp_min_blocks(int T, int EB) { return EB >= 16 ? (512 / T > 0 ? 512 / T : 1) : (T >= 512 ? 2 : 3); }
 
+// Tiles are double-buffered (the next tile's copies overlap this tile's
+// passes) except for 512-point lines of 16-byte elements: there one buffer
+// halves the shared memory, so four CTAs fit on an SM instead of three, and the
+// other CTAs cover the copy latency.
+template <class A, int N>
+constexpr bool warp_double_buffer() { return !(N >= 512 && sizeof(typename A::C) >= 16); }
+
 template <class A, int N, int G>
 __global__ void __launch_bounds__(32 * G, warp_min_blocks(32 * G, sizeof(typename A::C)))
 fft_warp_kernel(const StageArgs p, int64_t ntiles)
 {
     using C = typename A::C;
     constexpr int LS = warp_line_stride<sizeof(C)>(N);
+    constexpr bool DB = warp_double_buffer<A, N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* cur = reinterpret_cast<C*>(smem_raw);
-    C* nxt = cur + G * LS;
+    C* nxt = DB ? cur + G * LS : cur;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const typename A::W* tw = reinterpret_cast<const typename A::W*>(p.tw);
     const bool convert = Io<A>::kConverts && p.in_fmt == FMT_C128;
 
     int64_t tile = blockIdx.x;
-    if (tile < ntiles) warp_issue_load<A, N>(p, tile_geom(p, tile, G), warp, cur + warp * LS, lane);
+    if (DB && tile < ntiles) warp_issue_load<A, N>(p, tile_geom(p, tile, G), warp, cur + warp * LS, lane);
     for (; tile < ntiles; tile += gridDim.x) {
         const TileGeom tg = tile_geom(p, tile, G);
         C* line = cur + warp * LS;
+        if (!DB) warp_issue_load<A, N>(p, tg, warp, line, lane);
         cp_async_wait_all();
         if (convert) { if (p.conj_in) warp_fix<A, N, true, true>(line, lane); else warp_fix<A, N, true, false>(line, lane); }
         else if (p.conj_in) warp_fix<A, N, false, true>(line, lane);
         __syncwarp();
         const int64_t next = tile + gridDim.x;
-        if (next < ntiles) warp_issue_load<A, N>(p, tile_geom(p, next, G), warp, nxt + warp * LS, lane);
+        if (DB && next < ntiles) warp_issue_load<A, N>(p, tile_geom(p, next, G), warp, nxt + warp * LS, lane);
         WarpLine<A, N>::template passes<0>(line, tw, lane);
         __syncthreads();                   // every line of the tile is transformed
         warp_store_dispatch<A, N, G>(p, tg, cur, tid);
-        __syncthreads();                   // cur becomes the next prefetch target
+        __syncthreads();                   // cur becomes the next copy target
         C* t = cur; cur = nxt; nxt = t;
     }
     cp_async_wait_all();
@@ -236,7 +245,8 @@ template <class A, int N, int G>
 cudaError_t launch_warp_n(const StageLaunch& L, cudaStream_t st)
 {
     constexpr int T = 32 * G;
-    const size_t smem = 2 * (size_t)G * warp_line_stride<sizeof(typename A::C)>(N) * sizeof(typename A::C);
+    const size_t smem = (warp_double_buffer<A, N>() ? 2 : 1) * (size_t)G * warp_line_stride<sizeof(typename A::C)>(N) *
+                        sizeof(typename A::C);
     static int blocks_per_sm = -1;
     if (blocks_per_sm < 0) {
         int b = 0;
