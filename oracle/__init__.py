@@ -66,6 +66,8 @@ def _load():
             lib.oracle_redistribute.argtypes = [i64] * 4 + [i32, vp, vp, vp]
             lib.oracle_fft3d.restype = i32
             lib.oracle_fft3d.argtypes = [i64] * 4 + [i32, vp, vp, vp, vp]
+            lib.oracle_rfft3d.restype = i32
+            lib.oracle_rfft3d.argtypes = [i64] * 4 + [i32, vp, vp, vp, vp]
             _lib = lib
     return _lib
 
@@ -174,6 +176,37 @@ def fft3d(A, Na: int, Nb: int, Nc: int, Np: int, direction: int = FORWARD, count
     C1 = np.zeros((Np, Np), dtype=np.int64)
     C2 = np.zeros((Np, Np), dtype=np.int64)
     rc = _load().oracle_fft3d(Na, Nb, Nc, Np, direction, _ptr(A), _ptr(out), _ptr(C1), _ptr(C2))
+    if rc != 0:
+        raise ValueError("decomposition undefined for this (Na, Nb, Nc, Np)")
+    if counts:
+        return out, C1, C2
+    return out
+
+
+def rfft3d(A, Na: int, Nb: int, Nc: int, Np: int, direction: int = FORWARD, counts: bool = False):
+    """Real 3-D transform under the decomposition over Np ranks.
+
+    forward: A is the real abc-ordered array (N doubles); the result is the
+    half spectrum kc <= Nc/2 in cba order, [Nc//2 + 1][Nb][Na] flat complex.
+    backward: A is that half spectrum; the result is the real abc array
+    divided by N (the real part of the inverse of the Hermitian-extended
+    spectrum).  With ``counts`` also returns the count matrices of the two
+    transposes of the half array."""
+    Nch = Nc // 2 + 1
+    M = Na * Nb * Nch
+    if direction == FORWARD:
+        A = np.ascontiguousarray(np.asarray(A, dtype=np.float64).reshape(-1))
+        if A.size != Na * Nb * Nc:
+            raise ValueError("size mismatch")
+        out = np.empty(M, dtype=np.complex128)
+    else:
+        A = _c128(A).reshape(-1)
+        if A.size != M:
+            raise ValueError("size mismatch")
+        out = np.empty(Na * Nb * Nc, dtype=np.float64)
+    C1 = np.zeros((Np, Np), dtype=np.int64)
+    C2 = np.zeros((Np, Np), dtype=np.int64)
+    rc = _load().oracle_rfft3d(Na, Nb, Nc, Np, direction, _ptr(A), _ptr(out), _ptr(C1), _ptr(C2))
     if rc != 0:
         raise ValueError("decomposition undefined for this (Na, Nb, Nc, Np)")
     if counts:

@@ -26,7 +26,12 @@
  *   - forward = exp(-2 pi i ...), unnormalised; backward = exp(+2 pi i ...)
  *     with a final division by N, input in cba order, output in abc order,
  *     axes transformed a, b, c;
- *   - inside a send segment, elements are kept in ascending source index.
+ *   - inside a send segment, elements are kept in ascending source index;
+ *   - real transforms (future work in the paper): the real abc array is
+ *     decomposed with (Na, Nb, Nc), the complex half arrays of the later
+ *     stages with Nc replaced by Nc/2 + 1; the inverse keeps the real part of
+ *     the inverse DFT of the half spectrum extended by Hermitian symmetry
+ *     along c.
  *
  * Arithmetic: plain double, no compensated sums, so the FFT error grows like
  * u*log(n).  Twiddles are evaluated in long double and rounded once.
@@ -430,6 +435,103 @@ static int transform_stage(int layout, const int64_t n[3], int64_t Np, cplx* dat
         }
     free(W); free(buf); free(res); free(xs);
     return 0;
+}
+
+/* ---------------------------------------------- real transforms (R2C) -- */
+
+/* A real 3-D transform keeps the kc <= Nc/2 half of the spectrum: the rest
+ * follows from X[-ka,-kb,-kc] = conj X[ka,kb,kc].  The paper names real
+ * transforms as future work only.  Reading taken: the real abc array is
+ * decomposed by Eqs. 2-9 with (Na, Nb, Nc) and the complex arrays of the
+ * later stages by the same equations with Nc replaced by Nch = Nc/2 + 1
+ * (integer division): cab (Nch, Na, Nb), cba (Nch, Nb, Na).  Rank boxes are
+ * whole c-lines in both the real array and the half array, so a rank keeps
+ * the same lines across the first stage. */
+
+/* Stage 1, forward: every rank copies each real c-line of its box into a
+ * complex line buffer (imaginary parts 0), takes the 1-D DFT and keeps
+ * frequencies 0..Nch-1 as that line of the half array [Na][Nb][Nch]. */
+static int real_stage_forward(int64_t Na, int64_t Nb, int64_t Nc, int64_t Np, const double* x, cplx* half)
+{
+    const int64_t Nch = Nc / 2 + 1;
+    int64_t* xs = (int64_t*)malloc(sizeof(int64_t) * (size_t)(Np + 1));
+    if (oracle_boundaries(Na, Nb, Nc, Np, xs)) { free(xs); return -1; }
+    cplx* W = make_table(Nc, -1);
+    cplx* buf = (cplx*)malloc(sizeof(cplx) * (size_t)Nc);
+    cplx* res = (cplx*)malloc(sizeof(cplx) * (size_t)Nc);
+    for (int64_t r = 0; r < Np; ++r)
+        for (int64_t xx = xs[r]; xx < xs[r + 1]; xx += Nc) {
+            const int64_t l = xx / Nc;                             /* line (a, b) */
+            for (int64_t i = 0; i < Nc; ++i) { buf[i].re = x[xx + i]; buf[i].im = 0.0; }
+            fft_rec(Nc, buf, 1, res, W, Nc);
+            memcpy(half + l * Nch, res, sizeof(cplx) * (size_t)Nch);
+        }
+    free(W); free(buf); free(res); free(xs);
+    return 0;
+}
+
+/* Last stage of the inverse: each c-line of the half array [Na][Nb][Nch] is
+ * extended to the full spectrum, Z[k] = conj Z[Nc - k] for k >= Nch; the
+ * inverse DFT is taken and its real part kept (so only the real parts of
+ * Z[0] and, for even Nc, of Z[Nc/2] count). */
+static int real_stage_backward(int64_t Na, int64_t Nb, int64_t Nc, int64_t Np, const cplx* half, double* x)
+{
+    const int64_t Nch = Nc / 2 + 1;
+    int64_t* xs = (int64_t*)malloc(sizeof(int64_t) * (size_t)(Np + 1));
+    if (oracle_boundaries(Na, Nb, Nc, Np, xs)) { free(xs); return -1; }
+    cplx* W = make_table(Nc, 1);
+    cplx* buf = (cplx*)malloc(sizeof(cplx) * (size_t)Nc);
+    cplx* res = (cplx*)malloc(sizeof(cplx) * (size_t)Nc);
+    for (int64_t r = 0; r < Np; ++r)
+        for (int64_t xx = xs[r]; xx < xs[r + 1]; xx += Nc) {
+            const int64_t l = xx / Nc;
+            for (int64_t k = 0; k < Nc; ++k) {
+                if (k < Nch) buf[k] = half[l * Nch + k];
+                else { buf[k].re = half[l * Nch + Nc - k].re; buf[k].im = -half[l * Nch + Nc - k].im; }
+            }
+            fft_rec(Nc, buf, 1, res, W, Nc);
+            for (int64_t i = 0; i < Nc; ++i) x[xx + i] = res[i].re;
+        }
+    free(W); free(buf); free(res); free(xs);
+    return 0;
+}
+
+/* Real 3-D transform under the decomposition.
+ *   dir = -1: in = real abc array (Na*Nb*Nc doubles), out = half spectrum in
+ *             cba order [Nch][Nb][Na]; stages c (real), b, a.
+ *   dir = +1: in = half spectrum in cba order, out = real abc array divided
+ *             by N = Na*Nb*Nc; stages a, b, c (real).
+ * C1, C2 (may be NULL): count matrices of the two transposes of the half
+ * array. */
+int oracle_rfft3d(int64_t Na, int64_t Nb, int64_t Nc, int64_t Np, int dir,
+                  const void* in, void* out, int64_t* C1, int64_t* C2)
+{
+    const int64_t Nch = Nc / 2 + 1;
+    const int64_t nh[3] = {Na, Nb, Nch};
+    const int64_t M = Na * Nb * Nch, N = Na * Nb * Nc;
+    if (dir != -1 && dir != 1) return -1;
+    cplx* t0 = (cplx*)malloc(sizeof(cplx) * (size_t)M);
+    cplx* t1 = (cplx*)malloc(sizeof(cplx) * (size_t)M);
+    int rc = 0;
+    if (dir == -1) {
+        rc |= real_stage_forward(Na, Nb, Nc, Np, (const double*)in, t0);   /* along c, real */
+        rc |= redistribute(0, 1, nh, Np, t0, t1, C1);                     /* abc -> cab    */
+        rc |= transform_stage(1, nh, Np, t1, -1);                         /* along b       */
+        rc |= redistribute(1, 2, nh, Np, t1, t0, C2);                     /* cab -> cba    */
+        rc |= transform_stage(2, nh, Np, t0, -1);                         /* along a       */
+        memcpy(out, t0, sizeof(cplx) * (size_t)M);
+    } else {
+        memcpy(t0, in, sizeof(cplx) * (size_t)M);
+        rc |= transform_stage(2, nh, Np, t0, 1);                          /* along a       */
+        rc |= redistribute(2, 1, nh, Np, t0, t1, C1);                     /* cba -> cab    */
+        rc |= transform_stage(1, nh, Np, t1, 1);                          /* along b       */
+        rc |= redistribute(1, 0, nh, Np, t1, t0, C2);                     /* cab -> abc    */
+        double* x = (double*)out;
+        rc |= real_stage_backward(Na, Nb, Nc, Np, t0, x);                 /* along c, real */
+        for (int64_t i = 0; i < N; ++i) x[i] /= (double)N;
+    }
+    free(t0); free(t1);
+    return rc ? -1 : 0;
 }
 
 /* Full 3-D C2C transform under the decomposition.

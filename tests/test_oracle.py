@@ -274,3 +274,89 @@ def test_count_matrix_2d_cab_to_cba_half_local():
     box = Na * Nb * Nc // P
     assert np.all(np.diag(C2) == box // 2)
     assert C2.sum() == Na * Nb * Nc
+
+
+# ------------------------------------------------- real transforms (R2C) --
+# The half spectrum kc <= Nc/2 of a real input, with the complex stages
+# decomposed over (Na, Nb, Nc//2 + 1).  Pinned to numpy's rfftn / irfftn (the
+# special case of a library routine), to brute-force DFTs on tiny shapes, to
+# the complex oracle and to the round trip.
+
+R2C_SHAPES = [((4, 6, 8), 3), ((5, 3, 7), 2), ((8, 8, 8), 8), ((6, 5, 4), 5), ((3, 10, 9), 15),
+              ((16, 12, 10), 48), ((7, 7, 2), 14), ((2, 3, 1), 2)]
+
+
+def _half_cba(X_abc_half):
+    """[Na][Nb][Nch] -> flat cba-half order (index (kc*Nb + kb)*Na + ka)."""
+    return np.ascontiguousarray(np.transpose(X_abc_half, (2, 1, 0))).reshape(-1)
+
+
+@pytest.mark.parametrize("shape,P", R2C_SHAPES)
+def test_rfft3d_matches_numpy_rfftn(shape, P):
+    Na, Nb, Nc = shape
+    x = synth.uniform_pm1(synth.config_seed(11) + Na * Nb * Nc, Na * Nb * Nc).reshape(shape)
+    X = oracle.rfft3d(x, Na, Nb, Nc, P)
+    assert X.size == Na * Nb * (Nc // 2 + 1)
+    assert oracle.rel_l2(X, _half_cba(np.fft.rfftn(x))) < 1e-14
+
+
+@pytest.mark.parametrize("shape,P", R2C_SHAPES)
+def test_irfft3d_matches_numpy_irfftn_on_any_half_spectrum(shape, P):
+    """Inverse of an arbitrary (not Hermitian-consistent) half spectrum: the real
+    part of the inverse DFT of its Hermitian extension along c, which drops the
+    imaginary parts of kc = 0 and (even Nc) kc = Nc/2: numpy's convention."""
+    Na, Nb, Nc = shape
+    Nch = Nc // 2 + 1
+    H = synth.complex_field((Nch, Nb, Na), seed=synth.config_seed(12) + Nc).reshape(-1)
+    x = oracle.rfft3d(H, Na, Nb, Nc, P, oracle.BACKWARD)
+    ref = np.fft.irfftn(np.transpose(H.reshape(Nch, Nb, Na), (2, 1, 0)), s=(Na, Nb, Nc), axes=(0, 1, 2))
+    assert np.linalg.norm(x - ref.reshape(-1)) <= 1e-14 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("shape", [(2, 3, 4), (3, 2, 5), (4, 4, 1), (1, 5, 6), (3, 3, 3)])
+def test_rfft3d_brute_force(shape):
+    Na, Nb, Nc = shape
+    x = synth.uniform_pm1(synth.config_seed(13), Na * Nb * Nc).reshape(shape)
+    full = oracle.dft3d_brute(x.astype(np.complex128), oracle.FORWARD).reshape(shape)
+    for P in (1, 2, min(Na * Nb, (Nc // 2 + 1) * min(Na, Nb))):
+        X = oracle.rfft3d(x, Na, Nb, Nc, P)
+        assert oracle.rel_l2(X, _half_cba(full[:, :, : Nc // 2 + 1])) < 1e-14
+
+
+@pytest.mark.parametrize("shape,P", R2C_SHAPES[:5])
+def test_rfft3d_is_the_half_of_the_complex_transform(shape, P):
+    Na, Nb, Nc = shape
+    x = synth.uniform_pm1(synth.config_seed(14), Na * Nb * Nc).reshape(shape)
+    Y = oracle.fft3d(x.astype(np.complex128), Na, Nb, Nc, min(P, Nc * min(Na, Nb)), oracle.FORWARD)
+    Y = Y.reshape(Nc, Nb, Na)[: Nc // 2 + 1].reshape(-1)
+    assert oracle.rel_l2(oracle.rfft3d(x, Na, Nb, Nc, P), Y) < 1e-14
+
+
+@pytest.mark.parametrize("shape,P", R2C_SHAPES)
+def test_rfft3d_round_trip_and_hermitian_columns(shape, P):
+    Na, Nb, Nc = shape
+    x = synth.normal(synth.config_seed(15), Na * Nb * Nc).reshape(shape)
+    X = oracle.rfft3d(x, Na, Nb, Nc, P)
+    back = oracle.rfft3d(X, Na, Nb, Nc, P, oracle.BACKWARD)
+    assert np.linalg.norm(back - x.reshape(-1)) <= 1e-14 * np.linalg.norm(x)
+    # kc = 0 (and kc = Nc/2 for even Nc) is the 2-D DFT of a real array: Hermitian in (ka, kb)
+    Xh = X.reshape(Nc // 2 + 1, Nb, Na)
+    for kc in ([0, Nc // 2] if Nc % 2 == 0 else [0]):
+        col = Xh[kc]
+        mirror = np.conj(col[(-np.arange(Nb))[:, None] % Nb, (-np.arange(Na))[None, :] % Na])
+        assert np.max(np.abs(col - mirror)) <= 1e-13 * max(1.0, np.max(np.abs(col)))
+
+
+def test_rfft3d_counts_are_those_of_the_half_array():
+    Na, Nb, Nc, P = 12, 10, 16, 6
+    x = synth.uniform_pm1(synth.config_seed(16), Na * Nb * Nc)
+    _, C1, C2 = oracle.rfft3d(x, Na, Nb, Nc, P, counts=True)
+    _, D1, D2 = oracle.fft3d(np.zeros(Na * Nb * (Nc // 2 + 1), complex), Na, Nb, Nc // 2 + 1, P,
+                             oracle.FORWARD, counts=True)
+    assert np.array_equal(C1, D1) and np.array_equal(C2, D2)
+    assert C1.sum() == C2.sum() == Na * Nb * (Nc // 2 + 1)
+
+
+def test_rfft3d_rejects_p_beyond_the_half_orderings():
+    with pytest.raises(ValueError):
+        oracle.rfft3d(np.zeros(3 * 4 * 5), 3, 4, 5, 12)       # cab-half (3, 3, 4): 9 < 12
