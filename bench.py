@@ -386,6 +386,8 @@ def measure_forms(of, torch, plans_f64, x, y, z, n, stream, args):
         out["batch64"] = measure_batch(of, torch, stream)
     # non-power-of-two 120 x 144 x 160, P = 32: FP64 vs FP32 vs split tensor-core forms
     out["mixed_120x144x160"] = measure_mixed(of, torch, stream)
+    # real transforms at 256^3 against the complex transform
+    out["r2c_256cubed"] = measure_r2c(of, torch, stream)
     # 512^3 forward, FP64, P = 1024 (the large configuration)
     if not args.no_512:
         n5 = 512
@@ -558,6 +560,67 @@ def measure_learned(of, torch, stream, Ps=(64, 256, 1024), reps=5):
     out["max_regret"] = round(max(regrets), 4)
     out["target"] = "within 5% of exhaustive autotuning"
     del x, y
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_r2c(of, torch, stream, n=256, P=64, reps=5):
+    """Real transforms at n^3 (real abc array -> half spectrum [n/2+1][n][n] and
+    back), FP64-accurate and FP32, against the complex transform of the same
+    input.  GFLOP/s in the 2.5 N log2 N convention of real transforms;
+    algorithmic bytes: the real array read (write) once plus three passes of
+    the half array (stage 1 writes it, stages 2 and 3 read and write it)."""
+    from paper_1501_07350_gb300 import synth
+    N = n ** 3
+    Nh = (n // 2 + 1) * n * n
+    dev = torch.device("cuda", torch.cuda.current_device())
+    x64 = torch.from_numpy(synth.normal(synth.config_seed(2), N)).to(dev)
+    peak = load_peaks()[0]
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    out = {"shape": [n, n, n], "P": P, "flops": "2.5 N log2 N"}
+    for dtype, name, rt, ct, E, R in [(of.R2C_F64, "f64", torch.float64, torch.complex128, 16, 8),
+                                      (of.R2C_F32, "f32", torch.float32, torch.complex64, 8, 4)]:
+        x = x64.to(rt)
+        h = torch.empty(Nh, dtype=ct, device=dev)
+        xb = torch.empty_like(x)
+        plan = of.openfft_plan(n, n, n, P, dtype)
+        of.openfft_set_stream(plan, stream)
+        of.openfft_set_tuning(plan, of.TUNE_EXHAUSTIVE)
+        ms_f = timed(lambda: of.openfft_exec_r2c(plan, x, h))
+        ms_b = timed(lambda: of.openfft_exec_c2r(plan, h, xb))
+        of.openfft_sync(plan)
+        err = float(torch.linalg.vector_norm(xb - x) / torch.linalg.vector_norm(x))
+        alg = R * N + 5 * E * Nh
+        out[name] = {"r2c_ms": round(ms_f, 4), "c2r_ms": round(ms_b, 4),
+                     "r2c_gflops": round(2.5 * N * math.log2(N) / ms_f / 1e6, 1),
+                     "r2c_hbm_frac": round(alg / (ms_f * 1e-3) / 1e9 / peak, 4),
+                     "c2r_hbm_frac": round(alg / (ms_b * 1e-3) / 1e9 / peak, 4),
+                     "round_trip_rel_l2": err,
+                     "chosen": of.openfft_candidate(plan, of.openfft_current_candidate(plan))}
+        of.openfft_destroy(plan)
+        # the complex transform of the same (real) input, for comparison
+        xc = x.to(ct)
+        yc = torch.empty_like(xc)
+        cp = of.openfft_plan(n, n, n, P, of.C2C_F64 if dtype == of.R2C_F64 else of.C2C_F32)
+        of.openfft_set_stream(cp, stream)
+        of.openfft_set_tuning(cp, of.TUNE_EXHAUSTIVE)
+        out[name]["c2c_forward_ms"] = round(timed(lambda: of.openfft_exec_c2c(cp, xc, yc, of.FORWARD)), 4)
+        of.openfft_destroy(cp)
+        del x, h, xb, xc, yc
     torch.cuda.empty_cache()
     return out
 
@@ -743,6 +806,7 @@ def main():
     ap.add_argument("--no-512", dest="no_512", action="store_true", help="skip the 512^3 form")
     ap.add_argument("--no-batch", dest="no_batch", action="store_true", help="skip the batched form")
     ap.add_argument("--only-batch", dest="only_batch", action="store_true", help="time the batched form only")
+    ap.add_argument("--only-r2c", dest="only_r2c", action="store_true", help="time the real transforms only")
     ap.add_argument("--only-learned", dest="only_learned", action="store_true",
                     help="time the learned selector against exhaustive autotuning at 512^3 only")
     ap.add_argument("--only-mixed", dest="only_mixed", action="store_true",
@@ -775,6 +839,14 @@ def main():
         _build.build()
         torch.cuda.set_device(local_rank)
         print(json.dumps({"batch64": measure_batch(of, torch, torch.cuda.current_stream())}))
+        return
+    if args.only_r2c:
+        import torch
+        from paper_1501_07350_gb300 import _build
+        from paper_1501_07350_gb300 import openfft as of
+        _build.build()
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"r2c_256cubed": measure_r2c(of, torch, torch.cuda.current_stream())}))
         return
     if args.only_learned:
         import torch

@@ -50,7 +50,9 @@ enum {
     OPENFFT_C2C_F64 = 0,        /* complex128 in/out, FP64-accurate (<= 1e-12 rel. L2)   */
     OPENFFT_C2C_F32 = 1,        /* complex64 in/out, FP32 arithmetic                     */
     OPENFFT_C2C_SPLIT_BF16 = 2, /* complex64 in/out, tensor-core DFT-GEMM, bf16 hi/lo (<= 1e-4) */
-    OPENFFT_C2C_SPLIT_TF32 = 3  /* complex64 in/out, tensor-core DFT-GEMM, tf32 hi/lo (<= 1e-5) */
+    OPENFFT_C2C_SPLIT_TF32 = 3, /* complex64 in/out, tensor-core DFT-GEMM, tf32 hi/lo (<= 1e-5) */
+    OPENFFT_R2C_F64 = 4,        /* real transform: double in, complex128 half spectrum out (FP64-accurate) */
+    OPENFFT_R2C_F32 = 5         /* real transform: float in, complex64 half spectrum out (FP32) */
 };
 
 /* Sign of the exponent. */
@@ -137,6 +139,26 @@ openfft_plan_t openfft_plan(int Na, int Nb, int Nc, int P, int dtype);
  * Asynchronous on the plan's stream.  Returns OPENFFT_OK, INVALID_ARG,
  * ALIAS or CUDA. */
 int openfft_exec_c2c(openfft_plan_t plan, const void* in, void* out, int dir);
+
+/* Real transforms (plans of dtype OPENFFT_R2C_F64 / OPENFFT_R2C_F32).  The
+ * paper names real transforms as future work; they are built here on the same
+ * decomposition:
+ *   - input of openfft_exec_r2c: the real abc array [Na][Nb][Nc] (double or
+ *     float), rank r's box at openfft_box(plan, 0, r, ...) in real elements;
+ *   - output: the half spectrum X[ka][kb][kc], kc <= Nc/2, in cba order
+ *     [Nch][Nb][Na] with Nch = Nc/2 + 1 (complex128 or complex64); the
+ *     complex arrays are decomposed by Eqs. 2-9 with Nc replaced by Nch, so
+ *     rank r's output box is openfft_box(plan, 1, r, ...) in that array;
+ *   - openfft_exec_c2r takes such a half spectrum and writes the real abc
+ *     array: the real part of the inverse DFT of the spectrum extended by
+ *     Hermitian symmetry along c, divided by N = Na*Nb*Nc (only the real
+ *     parts of kc = 0 and, for even Nc, kc = Nc/2 count).
+ * P must satisfy P <= Na*Nb, P <= Nch*Na and P <= Nch*Nb (P_TOO_LARGE
+ * otherwise).  Device pointers, 16-byte aligned, in != out (ALIAS); the
+ * fused variant only.  openfft_exec_c2c on a real plan, or these on a
+ * complex plan, returns INVALID_ARG.  Asynchronous on the plan's stream. */
+int openfft_exec_r2c(openfft_plan_t plan, const void* in, void* out);
+int openfft_exec_c2r(openfft_plan_t plan, const void* in, void* out);
 
 /* Same transform with HOST buffers: copies `host_in` to plan-owned device
  * memory, executes, copies the result to `host_out` and waits.  Page-locked

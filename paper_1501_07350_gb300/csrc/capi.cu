@@ -121,6 +121,8 @@ struct openfft_plan_s {
     BatchPlan* batch = nullptr;   // set for plans made by openfft_plan_many
     int* d_status = nullptr;      // device status word of the tensor-core stages
     void* bimg[3] = {};           // DFT-GEMM operand images per axis (split dtypes)
+    bool real = false;            // real transform (OPENFFT_R2C_*): half arrays after stage 1
+    int Ncx = 0;                  // c extent of the complex arrays: Nc, or Nc / 2 + 1 for real plans
 };
 
 namespace {
@@ -190,6 +192,40 @@ int make_stage(openfft_plan_s* p, int axis, int arith, int Gt, int family, int64
     L.family = family;
     L.grid = a.ngroups * (group_i2 ? M1 : M2);
     L.smem = 2 * (size_t)n * (G + 1) * E;     // two ping-pong tiles
+    if (L.grid > 0x7fffffffLL) return fail(OPENFFT_ERR_UNSUPPORTED, "grid too large");
+    return OPENFFT_OK;
+}
+
+// The real stage of a real plan: forward = stage 1 (real c-lines -> half
+// spectra, stored transposed into the cab half array [Ncx][Na][Nb]), backward
+// = the last stage (abc half array [Na][Nb][Ncx] -> real c-lines, times 1/N).
+int make_real_stage(openfft_plan_s* p, int arith, int Gt, bool forward, int mid_fmt, StageLaunch& L)
+{
+    const int n = p->Nc;
+    const int E = elem_bytes_of(arith);
+    const int64_t lines = (int64_t)p->Na * p->Nb;
+    int G = Gt;
+    while (G > 1 && (int64_t)G >= lines) G /= 2;          // no more complex lines than line pairs
+    while (G > 1 && 2 * (size_t)n * (G + 1) * E > 200 * 1024) G /= 2;
+    if (2 * (size_t)n * (G + 1) * E > 200 * 1024) return fail(OPENFFT_ERR_UNSUPPORTED_RADIX, "axis too long for one CTA");
+    StageArgs& a = L.args;
+    std::memset(&a, 0, sizeof(a));
+    const int twf = arith == ARITH_F64 ? FMT_C128 : (arith == ARITH_F32 ? FMT_C64 : FMT_DF);
+    a.tw = p->tw[2][twf];
+    a.M1 = lines; a.M2 = 1;
+    a.S1 = 1; a.S2 = 0; a.Sk = lines;
+    a.ngroups = (lines + 2 * G - 1) / (2 * G);
+    a.scale = forward ? 1.0 : 1.0 / (double)p->N;
+    a.n = n; a.G = G; a.log2G = ilog2(G);
+    a.npass = (int)p->rad[2].size();
+    for (size_t i = 0; i < p->rad[2].size(); ++i) a.radix[i] = p->rad[2][i];
+    a.do_fft = 1;
+    const int real_fmt = arith == ARITH_F32 ? FMT_R32 : FMT_R64;
+    a.in_fmt = forward ? real_fmt : mid_fmt;
+    a.out_fmt = forward ? mid_fmt : real_fmt;
+    L.arith = arith; L.sms = p->sms; L.family = forward ? KERNEL_R2C : KERNEL_C2R; L.status = p->d_status;
+    L.grid = a.ngroups;
+    L.smem = 2 * (size_t)n * (G + 1) * E;
     if (L.grid > 0x7fffffffLL) return fail(OPENFFT_ERR_UNSUPPORTED, "grid too large");
     return OPENFFT_OK;
 }
@@ -270,6 +306,28 @@ int build_ops(openfft_plan_s* p, const Candidate& c)
     F.clear(); B.clear();
     StageLaunch L;
     int st;
+    if (p->real) {
+        // real transform, fused stores only; the complex stages run on the
+        // half arrays (c extent Ncx = Nc / 2 + 1)
+        if (c.variant != OPENFFT_VARIANT_FUSED) return fail(OPENFFT_ERR_UNSUPPORTED, "real plans run the fused variant");
+        const int64_t Nh = p->Ncx;
+        // forward: real c-lines -> cab half; b-lines of cab -> cba; a-lines of cba in place
+        if ((st = make_real_stage(p, ar, c.G, true, mid, L))) return st;
+        F.push_back(stage_op(B_IN, B_A, L));
+        if ((st = make_stage(p, 1, ar, c.G, c.family, Na, Nh, 1, Nb * Na, Na, 0, 0, mid, mid, 0, 0, 1.0, 1, L))) return st;
+        F.push_back(stage_op(B_A, B_OUT, L));
+        if ((st = make_stage(p, 0, ar, c.G, c.family, Nh * Nb, 1, Na, 0, 1, 0, 1, mid, ext, 0, 0, 1.0, 1, L))) return st;
+        F.push_back(stage_op(B_OUT, B_OUT, L));
+        // backward: a-lines of cba -> cab (conjugated on entry); b-lines of cab
+        // -> abc half [Na][Nb][Nh]; real c-lines out (times 1/N)
+        if ((st = make_stage(p, 0, ar, c.G, c.family, Nb, Nh, 1, Na * Nb, Nb, 0, 0, ext, mid, 1, 0, 1.0, 1, L))) return st;
+        B.push_back(stage_op(B_IN, B_A, L));
+        if ((st = make_stage(p, 1, ar, c.G, c.family, Na, Nh, Nb * Nh, 1, Nh, 1, 0, mid, mid, 0, 0, 1.0, 1, L))) return st;
+        B.push_back(stage_op(B_A, B_B, L));
+        if ((st = make_real_stage(p, ar, c.G, false, mid, L))) return st;
+        B.push_back(stage_op(B_B, B_OUT, L));
+        return OPENFFT_OK;
+    }
     if (c.variant == OPENFFT_VARIANT_FUSED) {
         // forward: c-lines of abc -> cab; b-lines of cab -> cba; a-lines of cba in place
         if ((st = make_stage(p, 2, ar, c.G, c.family, Na * Nb, 1, 1, 0, Na * Nb, 0, 0, ext, mid, 0, 0, 1.0, 1, L))) return st;
@@ -471,7 +529,7 @@ void candidate_features(const openfft_plan_s* p, const Candidate& c, float* f)
     f[0] = l2(p->Na) / 10.f; f[1] = l2(p->Nb) / 10.f; f[2] = l2(p->Nc) / 10.f;
     f[3] = l2((double)p->N) / 30.f;
     f[4] = l2(p->P) / 10.f;
-    f[5] = p->dtype == OPENFFT_C2C_F64 ? 1.f : 0.f;
+    f[5] = (p->dtype == OPENFFT_C2C_F64 || p->dtype == OPENFFT_R2C_F64) ? 1.f : 0.f;
     f[6] = 0.f;                                            // log2(batch) / 7, batch = 1
     f[7] = c.variant == OPENFFT_VARIANT_FUSED ? 1.f : 0.f;
     f[8] = c.variant == OPENFFT_VARIANT_PACK_UNPACK ? 1.f : 0.f;
@@ -514,7 +572,7 @@ int time_candidates(openfft_plan_s* p, std::vector<float>& ms)
         float best = 1e30f;
         for (int rep = 0; rep < 2 && !st; ++rep) {
             cudaEventRecord(e0, p->stream);
-            st = openfft_exec_c2c(p, tin, tout, OPENFFT_FORWARD);
+            st = p->real ? openfft_exec_r2c(p, tin, tout) : openfft_exec_c2c(p, tin, tout, OPENFFT_FORWARD);
             cudaEventRecord(e1, p->stream);
             cudaEventSynchronize(e1);
             float t = 0.f;
@@ -568,14 +626,21 @@ int openfft_decomp_counts(int Na, int Nb, int Nc, int P, int exchange, int64_t* 
 
 openfft_plan_t openfft_plan(int Na, int Nb, int Nc, int P, int dtype)
 {
-    if (validate_dims(Na, Nb, Nc, P)) return nullptr;
-    if (dtype < OPENFFT_C2C_F64 || dtype > OPENFFT_C2C_SPLIT_TF32) {
+    if (dtype < OPENFFT_C2C_F64 || dtype > OPENFFT_R2C_F32) {
         fail(OPENFFT_ERR_INVALID_ARG, "unknown dtype");
         return nullptr;
     }
-    const bool c64 = dtype != OPENFFT_C2C_F64;             // complex64 data
+    const bool real = dtype == OPENFFT_R2C_F64 || dtype == OPENFFT_R2C_F32;
+    // the complex arrays of a real plan are the half arrays (c extent Nc / 2 + 1)
+    const int Ncx = real ? Nc / 2 + 1 : Nc;
+    if (Nc < 1 || validate_dims(Na, Nb, Ncx, P)) {
+        if (Nc < 1) fail(OPENFFT_ERR_INVALID_ARG, "sizes and P must be >= 1");
+        return nullptr;
+    }
+    const bool c64 = dtype != OPENFFT_C2C_F64 && dtype != OPENFFT_R2C_F64;   // complex64 data
     openfft_plan_s* p = new openfft_plan_s();
     p->Na = Na; p->Nb = Nb; p->Nc = Nc; p->P = P; p->dtype = dtype;
+    p->real = real; p->Ncx = Ncx;
     p->N = (int64_t)Na * Nb * Nc;
     const int lens[3] = {Na, Nb, Nc};
     for (int ax = 0; ax < 3; ++ax)
@@ -633,7 +698,7 @@ openfft_plan_t openfft_plan(int Na, int Nb, int Nc, int P, int dtype)
     const int whichs[4] = {1, 2, -2, -1};
     for (int i = 0; i < 4; ++i) {
         TransposeTables& T = p->tt[i];
-        T.t = make_transpose(whichs[i], Na, Nb, Nc, P);
+        T.t = make_transpose(whichs[i], Na, Nb, Ncx, P);
         std::vector<int64_t> sb, rb, ch, sd, rd;
         build_transpose_tables(T.t, T.C, sb, rb, ch, 8192, &sd, &rd);
         T.nchunks = (int64_t)ch.size() / 3;
@@ -666,13 +731,21 @@ openfft_plan_t openfft_plan(int Na, int Nb, int Nc, int P, int dtype)
     // default kernel.  The first candidate is the default.
     {
         std::vector<int> ariths;
-        if (dtype == OPENFFT_C2C_F32) ariths = {ARITH_F32};
+        if (dtype == OPENFFT_C2C_F32 || dtype == OPENFFT_R2C_F32) ariths = {ARITH_F32};
         else if (dtype == OPENFFT_C2C_SPLIT_TF32) ariths = {ARITH_TC_TF32};
         else if (dtype == OPENFFT_C2C_SPLIT_BF16) ariths = {ARITH_TC_BF16};
         else ariths = {ARITH_DF, ARITH_F64};
         const bool f32 = c64;
         const int gw = f32 ? 16 : 8, gn = f32 ? 8 : 4;
         for (int ar : ariths) {
+            if (real) {                    // real plans: the fused variant with every kernel family
+                p->cands.push_back(Candidate{OPENFFT_VARIANT_FUSED, ar, gw, KERNEL_AUTO});
+                p->cands.push_back(Candidate{OPENFFT_VARIANT_FUSED, ar, gn, KERNEL_AUTO});
+                p->cands.push_back(Candidate{OPENFFT_VARIANT_FUSED, ar, gw, KERNEL_TILE});
+                p->cands.push_back(Candidate{OPENFFT_VARIANT_FUSED, ar, gn, KERNEL_TILE});
+                p->cands.push_back(Candidate{OPENFFT_VARIANT_FUSED, ar, gw, KERNEL_GENERIC});
+                continue;
+            }
             if (is_tc(ar)) {               // the DFT-GEMM form: fused stores only, tiles of 8 / 16 / 4 lines
                 for (int g : {8, 16, 4}) p->cands.push_back(Candidate{OPENFFT_VARIANT_FUSED, ar, g, KERNEL_AUTO});
                 continue;
@@ -712,10 +785,29 @@ int openfft_exec_c2c(openfft_plan_t plan, const void* in, void* out, int dir)
 {
     if (!plan || !in || !out) return fail(OPENFFT_ERR_INVALID_ARG, "null plan or buffer");
     if (plan->batch) return fail(OPENFFT_ERR_INVALID_ARG, "batched plan: use openfft_exec_many");
+    if (plan->real) return fail(OPENFFT_ERR_INVALID_ARG, "real plan: use openfft_exec_r2c / openfft_exec_c2r");
     if (in == out) return fail(OPENFFT_ERR_ALIAS, "in and out must differ (out-of-place only)");
     if (dir != OPENFFT_FORWARD && dir != OPENFFT_BACKWARD) return fail(OPENFFT_ERR_INVALID_ARG, "dir must be -1 or +1");
     const Candidate& c = plan->cands[(size_t)plan->current];
     return run_ops(plan, dir == OPENFFT_FORWARD ? plan->ops_fwd : plan->ops_bwd, in, out, c.arith);
+}
+
+int openfft_exec_r2c(openfft_plan_t plan, const void* in, void* out)
+{
+    if (!plan || !in || !out) return fail(OPENFFT_ERR_INVALID_ARG, "null plan or buffer");
+    if (!plan->real) return fail(OPENFFT_ERR_INVALID_ARG, "not a real plan (OPENFFT_R2C_*)");
+    if (in == out) return fail(OPENFFT_ERR_ALIAS, "in and out must differ (out-of-place only)");
+    const Candidate& c = plan->cands[(size_t)plan->current];
+    return run_ops(plan, plan->ops_fwd, in, out, c.arith);
+}
+
+int openfft_exec_c2r(openfft_plan_t plan, const void* in, void* out)
+{
+    if (!plan || !in || !out) return fail(OPENFFT_ERR_INVALID_ARG, "null plan or buffer");
+    if (!plan->real) return fail(OPENFFT_ERR_INVALID_ARG, "not a real plan (OPENFFT_R2C_*)");
+    if (in == out) return fail(OPENFFT_ERR_ALIAS, "in and out must differ (out-of-place only)");
+    const Candidate& c = plan->cands[(size_t)plan->current];
+    return run_ops(plan, plan->ops_bwd, in, out, c.arith);
 }
 
 int openfft_exec_c2c_host(openfft_plan_t plan, const void* host_in, void* host_out, int dir)
@@ -763,7 +855,9 @@ int openfft_box(openfft_plan_t plan, int which, int rank, int64_t start[3], int6
 {
     if (!plan) return fail(OPENFFT_ERR_INVALID_ARG, "null plan");
     if (which != 0 && which != 1) return fail(OPENFFT_ERR_INVALID_ARG, "which must be 0 (abc) or 1 (cba)");
-    return box_of(ordering_of(which == 0 ? ABC : CBA, plan->Na, plan->Nb, plan->Nc, plan->P),
+    // real plans: the input box is in the real abc array, the output box in
+    // the cba half array (c extent Nc / 2 + 1)
+    return box_of(ordering_of(which == 0 ? ABC : CBA, plan->Na, plan->Nb, which == 0 ? plan->Nc : plan->Ncx, plan->P),
                   rank, start, end, offset, count);
 }
 

@@ -109,6 +109,7 @@ cudaError_t stage_kernels_init(int max_dyn_smem)
 
 cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st)
 {
+    if (L.family == KERNEL_R2C || L.family == KERNEL_C2R) return launch_real_stage(L, st);
     if (L.arith == ARITH_TC_TF32 || L.arith == ARITH_TC_BF16) return launch_dftgemm(L, st, L.status);
     bool handled = false;
     cudaError_t e = cudaSuccess;

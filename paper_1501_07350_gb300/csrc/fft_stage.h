@@ -10,8 +10,8 @@ constexpr int kMaxLinesPerCta = 32;    // G <= 32
 constexpr int kMaxPasses = 16;
 constexpr int kMaxLen = 2048;          // longest supported axis (two tiles of one line fit in smem)
 
-// element formats in global memory
-enum { FMT_C128 = 0, FMT_C64 = 1, FMT_DF = 2 };
+// element formats in global memory (real arrays of the real transform: R64 / R32)
+enum { FMT_C128 = 0, FMT_C64 = 1, FMT_DF = 2, FMT_R64 = 3, FMT_R32 = 4 };
 // arithmetic: FP64, FP32, double-float, and the split-precision tensor-core
 // DFT-GEMM forms (complex64 data)
 enum { ARITH_F64 = 0, ARITH_F32 = 1, ARITH_DF = 2, ARITH_TC_TF32 = 3, ARITH_TC_BF16 = 4 };
@@ -50,6 +50,10 @@ struct StageLaunch {
 // stage kernel families: warp-per-line (power-of-two n), tile (specialised n),
 // generic (any n); AUTO takes the first that has an instantiation for (n, G)
 enum { KERNEL_AUTO = 0, KERNEL_WARP = 1, KERNEL_TILE = 2, KERNEL_GENERIC = 3 };
+// the real stages of the real transform (r2c.cu): the forward stage 1 and the
+// inverse's last stage; M1 = number of real lines, G = complex lines per CTA
+enum { KERNEL_R2C = 4, KERNEL_C2R = 5 };
+cudaError_t launch_real_stage(const StageLaunch& L, cudaStream_t st);
 
 cudaError_t stage_kernels_init(int max_dyn_smem);
 // Resident CTAs per SM of a persistent kernel with `threads` threads and

@@ -1,0 +1,219 @@
+// r2c.cu -- the real stages of the real 3-D transform (OPENFFT_R2C_F64 /
+// OPENFFT_R2C_F32): the first stage of the forward transform (real c-lines ->
+// half spectra, frequencies 0..n/2) and the last stage of the inverse (half
+// spectra -> real c-lines).  The complex stages in between are the ordinary
+// stage kernels run on the half arrays.
+//
+// Two real lines travel as one complex line z = x1 + i x2.
+//   Forward: Z = DFT(z); with Zr[k] = conj Z[(n - k) mod n] the two spectra
+//   are X1 = (Z + Zr) / 2 and X2 = -i (Z - Zr) / 2, and their frequencies
+//   0..n/2 are stored, transposed, into the half array of the next ordering.
+//   Inverse: the inverse pipeline conjugates on entry, so the half spectrum V
+//   that reaches this stage gives the real line as the forward DFT of V's
+//   Hermitian extension (a real result: the exit conjugation is void).  The
+//   complex line is Z[k] = V1[k] + i V2[k] and Z[n - k] = conj V1[k] +
+//   i conj V2[k] for 0 < k < n - k; Z[0] and, for even n, Z[n/2] take the real
+//   parts of V1 and V2 only.  Re and Im of DFT(Z), times the scale, are the
+//   two real lines.
+//
+// One CTA per tile of 2G real lines (G complex lines) in two ping-pong
+// [n][G + 1] shared-memory tiles; the radix passes are those of the generic
+// stage kernel (any supported n, runtime radix plan).
+#include <cuda_runtime.h>
+
+#include "fft_stage.h"
+#include "generic_stage.cuh"
+#include "stage_io.cuh"
+
+namespace ofg {
+
+namespace {
+
+// Two real values <-> one complex element, per arithmetic.
+template <class A> struct RealPair;
+
+template <> struct RealPair<ArF64> {
+    using T = double;
+    __device__ __forceinline__ static double2 make(double a, double b) { return make_double2(a, b); }
+    __device__ __forceinline__ static double2 re_parts(double2 u, double2 v) { return make_double2(u.x, v.x); }
+    __device__ __forceinline__ static double part(double2 z, int im, double s) { return (im ? z.y : z.x) * s; }
+};
+
+template <> struct RealPair<ArF32> {
+    using T = float;
+    __device__ __forceinline__ static float2 make(float a, float b) { return make_float2(a, b); }
+    __device__ __forceinline__ static float2 re_parts(float2 u, float2 v) { return make_float2(u.x, v.x); }
+    __device__ __forceinline__ static float part(float2 z, int im, double s) { return (im ? z.y : z.x) * (float)s; }
+};
+
+// double-float: (re.hi, im.hi, re.lo, im.lo)
+template <> struct RealPair<ArDF> {
+    using T = double;
+    __device__ __forceinline__ static float4 make(double a, double b) {
+        const float2 ha = split_f64(a), hb = split_f64(b);
+        return make_float4(ha.x, hb.x, ha.y, hb.y);
+    }
+    __device__ __forceinline__ static float4 re_parts(float4 u, float4 v) { return make_float4(u.x, v.x, u.z, v.z); }
+    __device__ __forceinline__ static double part(float4 z, int im, double s) {
+        return (im ? join_f64(z.y, z.w) : join_f64(z.x, z.z)) * s;
+    }
+};
+
+// i z, by exact sign changes: conj(-i conj z)
+template <class A>
+__device__ __forceinline__ typename A::C mul_i(typename A::C z) { return A::conj(A::mul_mi(A::conj(z))); }
+
+// The radix passes of the generic stage on a [n][G + 1] tile; returns the
+// tile that holds the result.
+template <class A>
+__device__ __forceinline__ const typename A::C* tile_passes(const StageArgs& p, typename A::C* buf0,
+                                                            typename A::C* buf1, int ld)
+{
+    using C = typename A::C;
+    const int tid = threadIdx.x, n = p.n;
+    const int g = tid & (p.G - 1), slot = tid >> p.log2G, slots = kStageThreads >> p.log2G;
+    C* a = buf0 + g;
+    C* b = buf1 + g;
+    const typename A::W* tw = reinterpret_cast<const typename A::W*>(p.tw);
+    int m = 1;
+    for (int ps = 0; ps < p.npass; ++ps) {
+        const int r = p.radix[ps];
+        const int s = n / (m * r);
+        switch (r) {
+        case 8: radix_pass<A, 8>(a, b, ld, n, m, s, slot, slots, tw); break;
+        case 4: radix_pass<A, 4>(a, b, ld, n, m, s, slot, slots, tw); break;
+        case 2: radix_pass<A, 2>(a, b, ld, n, m, s, slot, slots, tw); break;
+        case 3: radix_pass<A, 3>(a, b, ld, n, m, s, slot, slots, tw); break;
+        case 5: radix_pass<A, 5>(a, b, ld, n, m, s, slot, slots, tw); break;
+        default: radix_pass<A, 7>(a, b, ld, n, m, s, slot, slots, tw); break;
+        }
+        m *= r;
+        C* t = a; a = b; b = t;
+    }
+    return a - g;
+}
+
+// Forward real stage.  Real line l (l < p.M1) at in + l n; output element
+// (line l, frequency k <= n/2) at out[k Sk + l S1] in p.out_fmt.
+template <class A>
+__global__ void __launch_bounds__(kStageThreads) r2c_stage_kernel(const StageArgs p)
+{
+    using C = typename A::C;
+    using RP = RealPair<A>;
+    using T = typename RP::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tid = threadIdx.x, G = p.G, ld = G + 1, n = p.n;
+    C* buf0 = reinterpret_cast<C*>(smem_raw);
+    C* buf1 = buf0 + (size_t)n * ld;
+    const int64_t L = p.M1, l0 = (int64_t)blockIdx.x * 2 * G;
+    const T* x = reinterpret_cast<const T*>(p.in);
+    {   // real lines l0 + 2j, l0 + 2j + 1 -> complex line j
+        const int dj = kStageThreads / n, di = kStageThreads - dj * n;
+        int j = tid / n, i = tid - j * n;
+        for (int e = tid; e < G * n; e += kStageThreads) {
+            const int64_t la = l0 + 2 * j;
+            const T a = la < L ? x[la * n + i] : T(0);
+            const T b = la + 1 < L ? x[(la + 1) * n + i] : T(0);
+            buf0[i * ld + j] = RP::make(a, b);
+            i += di; j += dj;
+            if (i >= n) { i -= n; ++j; }
+        }
+    }
+    __syncthreads();
+    const C* cur = tile_passes<A>(p, buf0, buf1, ld);
+    // separate the two spectra, frequencies 0..n/2 of 2G lines
+    const int nh = n / 2 + 1, lg2 = p.log2G + 1;
+    for (int e = tid; e < (nh << lg2); e += kStageThreads) {
+        const int k = e >> lg2, o = e & ((1 << lg2) - 1);
+        const int64_t l = l0 + o;
+        if (l >= L) continue;
+        const int j = o >> 1;
+        const C z = cur[k * ld + j];
+        const C zr = A::conj(cur[(k == 0 ? 0 : n - k) * ld + j]);
+        const C X = A::scale((o & 1) ? A::mul_mi(A::sub(z, zr)) : A::add(z, zr), 0.5);
+        Io<A>::store(p.out, p.out_fmt, (int64_t)k * p.Sk + l * p.S1, X);
+    }
+}
+
+// Inverse real stage.  Half line l (l < p.M1) at in + l (n/2 + 1), in
+// p.in_fmt; real line l at out + l n, times p.scale.
+template <class A>
+__global__ void __launch_bounds__(kStageThreads) c2r_stage_kernel(const StageArgs p)
+{
+    using C = typename A::C;
+    using RP = RealPair<A>;
+    using T = typename RP::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tid = threadIdx.x, G = p.G, ld = G + 1, n = p.n, nh = n / 2 + 1;
+    C* buf0 = reinterpret_cast<C*>(smem_raw);
+    C* buf1 = buf0 + (size_t)n * ld;
+    const int64_t L = p.M1, l0 = (int64_t)blockIdx.x * 2 * G;
+    {   // half lines l0 + 2j, l0 + 2j + 1 -> Hermitian-extended complex line j
+        const int dj = kStageThreads / nh, dk = kStageThreads - dj * nh;
+        int j = tid / nh, k = tid - j * nh;
+        for (int e = tid; e < G * nh; e += kStageThreads) {
+            const int64_t la = l0 + 2 * j;
+            const C v1 = la < L ? Io<A>::load(p.in, p.in_fmt, la * nh + k) : A::zero();
+            const C v2 = la + 1 < L ? Io<A>::load(p.in, p.in_fmt, (la + 1) * nh + k) : A::zero();
+            if (k == 0 || 2 * k == n) {
+                buf0[k * ld + j] = RP::re_parts(v1, v2);
+            } else {
+                buf0[k * ld + j] = A::add(v1, mul_i<A>(v2));
+                buf0[(n - k) * ld + j] = A::add(A::conj(v1), mul_i<A>(A::conj(v2)));
+            }
+            k += dk; j += dj;
+            if (k >= nh) { k -= nh; ++j; }
+        }
+    }
+    __syncthreads();
+    const C* cur = tile_passes<A>(p, buf0, buf1, ld);
+    T* y = reinterpret_cast<T*>(p.out);
+    {   // Re / Im of complex line j -> real lines l0 + 2j / l0 + 2j + 1
+        const int dout = kStageThreads / n, di = kStageThreads - dout * n;
+        int o = tid / n, i = tid - o * n;
+        for (int e = tid; e < 2 * G * n; e += kStageThreads) {
+            const int64_t l = l0 + o;
+            if (l < L) y[l * n + i] = (T)RP::part(cur[i * ld + (o >> 1)], o & 1, p.scale);
+            i += di; o += dout;
+            if (i >= n) { i -= n; ++o; }
+        }
+    }
+}
+
+template <class A>
+cudaError_t launch_real_a(const StageLaunch& L, cudaStream_t st)
+{
+    static bool attr_r2c = false, attr_c2r = false;
+    const unsigned grid = (unsigned)L.grid;
+    if (L.family == KERNEL_R2C) {
+        if (!attr_r2c) {
+            cudaError_t e = cudaFuncSetAttribute(r2c_stage_kernel<A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 200 * 1024);
+            if (e) return e;
+            attr_r2c = true;
+        }
+        r2c_stage_kernel<A><<<grid, kStageThreads, L.smem, st>>>(L.args);
+    } else {
+        if (!attr_c2r) {
+            cudaError_t e = cudaFuncSetAttribute(c2r_stage_kernel<A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 200 * 1024);
+            if (e) return e;
+            attr_c2r = true;
+        }
+        c2r_stage_kernel<A><<<grid, kStageThreads, L.smem, st>>>(L.args);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_real_stage(const StageLaunch& L, cudaStream_t st)
+{
+    switch (L.arith) {
+    case ARITH_F64: return launch_real_a<ArF64>(L, st);
+    case ARITH_F32: return launch_real_a<ArF32>(L, st);
+    default: return launch_real_a<ArDF>(L, st);
+    }
+}
+
+}  // namespace ofg

@@ -21,6 +21,7 @@ ERR_INVALID_ARG, ERR_P_TOO_LARGE, ERR_UNSUPPORTED_RADIX, ERR_CUDA, ERR_NOMEM = 1
 ERR_TIMEOUT, ERR_ALIAS, ERR_UNSUPPORTED = 6, 7, 8
 
 C2C_F64, C2C_F32, C2C_SPLIT_BF16, C2C_SPLIT_TF32 = 0, 1, 2, 3
+R2C_F64, R2C_F32 = 4, 5
 FORWARD, BACKWARD = -1, 1
 VARIANT_PACK_EXCHANGE_UNPACK, VARIANT_PACK_UNPACK, VARIANT_FUSED = 0, 1, 2
 VARIANT_ISEND_WAITALL, VARIANT_ISEND_WAITALL_BLOCK, VARIANT_ISEND_WAITSOME_BLOCK, VARIANT_SENDRECV = 3, 4, 5, 6
@@ -42,7 +43,7 @@ EXPORTS = [
     "openfft_plan_many", "openfft_exec_many", "openfft_batch_debug",
     "openfft_mlp_num_params", "openfft_mlp_predict", "openfft_mlp_loss_grad", "openfft_mlp_train",
     "openfft_num_features", "openfft_candidate_features", "openfft_tune_times", "openfft_set_cost_model",
-    "openfft_tc_gemm",
+    "openfft_tc_gemm", "openfft_exec_r2c", "openfft_exec_c2r",
 ]
 
 _lock = threading.Lock()
@@ -77,6 +78,8 @@ def load():
         sig = {
             "openfft_plan": (vp, [i32, i32, i32, i32, i32]),
             "openfft_exec_c2c": (i32, [vp, vp, vp, i32]),
+            "openfft_exec_r2c": (i32, [vp, vp, vp]),
+            "openfft_exec_c2r": (i32, [vp, vp, vp]),
             "openfft_exec_c2c_host": (i32, [vp, vp, vp, i32]),
             "openfft_destroy": (None, [vp]),
             "openfft_sync": (i32, [vp]),
@@ -144,6 +147,16 @@ def openfft_plan(Na: int, Nb: int, Nc: int, P: int, dtype: int) -> int:
 
 def openfft_exec_c2c(plan: int, inp, out, direction: int) -> None:
     _check(load().openfft_exec_c2c(plan, _ptr(inp), _ptr(out), direction))
+
+
+def openfft_exec_r2c(plan: int, inp, out) -> None:
+    """Real abc array (float64 / float32) -> half spectrum [Nc//2+1][Nb][Na] (complex)."""
+    _check(load().openfft_exec_r2c(plan, _ptr(inp), _ptr(out)))
+
+
+def openfft_exec_c2r(plan: int, inp, out) -> None:
+    """Half spectrum [Nc//2+1][Nb][Na] -> real abc array, divided by N."""
+    _check(load().openfft_exec_c2r(plan, _ptr(inp), _ptr(out)))
 
 
 def openfft_exec_c2c_host(plan: int, host_in: np.ndarray, host_out: np.ndarray, direction: int) -> None:
