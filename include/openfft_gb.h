@@ -277,7 +277,7 @@ int openfft_num_features(void);
 int openfft_candidate_features(openfft_plan_t plan, int index, float* features);
 /* Time every candidate of `plan` twice (the faster run is kept) on
  * plan-owned buffers; ms[i] = -1 for a candidate that cannot run.  This is the
- * dataset writer of the learned model and the judge of its regret.  The
+ * dataset writer of the learned model and the reference of its regret.  The
  * current selection is kept. */
 int openfft_tune_times(openfft_plan_t plan, float* ms);
 /* Install (params != NULL, count >= 1) or remove (params == NULL) the

@@ -2,7 +2,7 @@
 
 The paper's tuner runs every communication method twice during
 initialisation and keeps the fastest.  Here that exhaustive timing becomes the
-dataset writer and the judge: ``collect`` times every candidate of many
+dataset writer and the reference of the regret: ``collect`` times every candidate of many
 problems (``openfft_tune_times``), ``train`` fits the cost model on the GPU with
 the library's own kernels (``openfft_mlp_train``), and ``evaluate`` reports,
 per held-out problem, the regret t(learned pick) / t(exhaustive best) - 1, the
