@@ -15,7 +15,7 @@ def pytest_configure(config):
 
 def pytest_collection_modifyitems(config, items):
     # GPU tests are skipped (not failed) on machines without a GPU only when the
-    # run did not ask for them explicitly; `-m gpu` on a GPU machine runs them.
+    # run did not ask for them explicitly; `-m gpu` on a machine with a GPU runs them.
     try:
         import torch
         has_gpu = torch.cuda.is_available()
