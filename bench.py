@@ -362,6 +362,41 @@ def measure_forms(of, torch, plans_f64, x, y, z, n, stream, args):
                 ms = time_exec(h, x, y, of.FORWARD)
                 out["f64_doublefloat_%s" % name] = {"ms": round(ms, 4), "gflops": round(flops(N) / ms / 1e6, 1)}
     of.openfft_set_tuning(h, of.TUNE_USER, cur)
+    # the paper's communication methods as transpose variants (Sec. 3.2.1), double-float
+    # arithmetic, at every P of the workload: which one wins where
+    names = {of.VARIANT_PACK_EXCHANGE_UNPACK: "Alltoallv (V0: pack, exchange, unpack)",
+             of.VARIANT_PACK_UNPACK: "Isend_Waitsome (V1: unpack from the send segments)",
+             of.VARIANT_ISEND_WAITALL: "Isend_Waitall (P exchange steps)",
+             of.VARIANT_ISEND_WAITALL_BLOCK: "Isend_Waitall_Block (B_SIZE = 32 groups)",
+             of.VARIANT_ISEND_WAITSOME_BLOCK: "Isend_Waitsome_Block",
+             of.VARIANT_SENDRECV: "Sendrecv (P shifted steps)",
+             of.VARIANT_FUSED: "fused into the stage stores (V2)"}
+    methods = {}
+    for P, hp in plans_f64.items():
+        curp = of.openfft_current_candidate(hp)
+        row = {}
+        for ci in range(of.openfft_num_candidates(hp)):
+            c = of.openfft_candidate(hp, ci)
+            if c["arith"] != of.ARITH_DOUBLE_FLOAT or c["kernel"] != 0 or c["lines_per_cta"] != 8:
+                continue
+            of.openfft_set_tuning(hp, of.TUNE_USER, ci)
+            row[names[c["variant"]]] = round(time_exec(hp, x, y, of.FORWARD, reps=3), 4)
+        of.openfft_set_tuning(hp, of.TUNE_USER, curp)
+        methods[str(P)] = {"ms": row, "fastest": min(row, key=row.get),
+                           "fastest_explicit": min((k for k in row if "V2" not in k), key=row.get)}
+    out["exchange_methods_256cubed_fwd"] = methods
+    # the small configuration: 32^3 complex128, P = 4, one forward transform (latency-bound)
+    from paper_1501_07350_gb300 import synth as _synth
+    xs = torch.from_numpy(_synth.complex_field((32, 32, 32), seed=_synth.config_seed(1))).to(x.device)
+    ys = torch.empty_like(xs)
+    hs = of.openfft_plan(32, 32, 32, 4, of.C2C_F64)
+    of.openfft_set_stream(hs, stream)
+    of.openfft_set_tuning(hs, of.TUNE_EXHAUSTIVE)
+    ms_s = time_exec(hs, xs, ys, of.FORWARD, reps=20)
+    out["small_32cubed_P4_fwd"] = {"us": round(ms_s * 1e3, 2), "gflops": round(flops(32 ** 3) / ms_s / 1e6, 2),
+                                   "chosen": of.openfft_candidate(hs, of.openfft_current_candidate(hs)),
+                                   "note": "latency-bound (3 launches of 512 KiB); no roofline fraction"}
+    of.openfft_destroy(hs)
     # FP32 form (complex64), auto-tuned
     x32 = x.to(torch.complex64)
     y32 = torch.empty_like(x32)

@@ -107,8 +107,9 @@ int64_t num_steps(int sched, int64_t P, int64_t B)
     return P;
 }
 
-// one CTA per pair of the step: copy segment (r, s) from its send
-// displacement to its receive displacement
+// blockIdx.x: pair of the step; blockIdx.y (of gridDim.y): share of the pair,
+// so that a step with few pairs still spreads over the GPU.  Copy segment
+// (r, s) from its send displacement to its receive displacement.
 template <class E>
 __global__ void segment_exchange_kernel(int sched, int64_t P, int64_t B, int64_t step,
                                         const int64_t* __restrict__ C, const int64_t* __restrict__ sdispl,
@@ -121,13 +122,15 @@ __global__ void segment_exchange_kernel(int sched, int64_t P, int64_t B, int64_t
     const int64_t len = C[r * P + s];
     const E* src = send + sdispl[r * P + s];
     E* dst = recv + rdispl[s * P + r];
-    for (int64_t j = threadIdx.x; j < len; j += blockDim.x) dst[j] = src[j];
+    const int64_t stride = (int64_t)gridDim.y * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; j < len; j += stride) dst[j] = src[j];
 }
 
-// one CTA per pair of the step: the receiver takes the elements of segment
-// (r, s) straight from the sender's send buffer and writes them to their
-// places in the destination ordering (unpack on arrival).  Threads walk the
-// source rows of rank r; each row holds a contiguous run of elements for s.
+// blockIdx.x: pair of the step, blockIdx.y: share of it.  The receiver takes
+// the elements of segment (r, s) straight from the sender's send buffer and
+// writes them to their places in the destination ordering (unpack on
+// arrival).  Threads walk the source rows of rank r; each row holds a
+// contiguous run of elements for s.
 template <class E>
 __global__ void segment_unpack_kernel(const Transpose t, int sched, int64_t B, int64_t step,
                                       const E* __restrict__ send, E* __restrict__ dst,
@@ -140,7 +143,8 @@ __global__ void segment_unpack_kernel(const Transpose t, int sched, int64_t B, i
     const int64_t R0 = row_begin(t.src, r), R1 = row_begin(t.src, r + 1);
     const int64_t Q0 = row_begin(t.dst, s), Q1 = row_begin(t.dst, s + 1);
     const int64_t base = sbase[r * P + s];
-    for (int64_t q = R0 + threadIdx.x; q < R1; q += blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.y * blockDim.x;
+    for (int64_t q = R0 + (int64_t)blockIdx.y * blockDim.x + threadIdx.x; q < R1; q += stride) {
         int64_t e_lo, cnt;
         row_range(t, q, Q0, Q1, &e_lo, &cnt);
         if (cnt <= 0) continue;
@@ -149,11 +153,27 @@ __global__ void segment_unpack_kernel(const Transpose t, int sched, int64_t B, i
     }
 }
 
+// Shares per pair: enough CTAs for four per SM over the pairs of a step.
+static dim3 step_grid(int64_t pairs)
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 1;
+    }
+    int64_t y = (4 * (int64_t)sms + pairs - 1) / pairs;
+    if (y < 1) y = 1;
+    if (y > 1024) y = 1024;
+    return dim3((unsigned)pairs, (unsigned)y);
+}
+
 cudaError_t launch_segment_exchange(int sched, int64_t P, int64_t B, int64_t step, int elem_bytes,
                                     const int64_t* C, const int64_t* sdispl, const int64_t* rdispl,
                                     const void* send, void* recv, cudaStream_t st)
 {
-    const unsigned grid = (unsigned)pairs_per_step(sched, P, B);
+    const dim3 grid = step_grid(pairs_per_step(sched, P, B));
     if (elem_bytes == 16)
         segment_exchange_kernel<uint4><<<grid, 128, 0, st>>>(sched, P, B, step, C, sdispl, rdispl,
                                                              (const uint4*)send, (uint4*)recv);
@@ -166,7 +186,7 @@ cudaError_t launch_segment_exchange(int sched, int64_t P, int64_t B, int64_t ste
 cudaError_t launch_segment_unpack(const Transpose& t, int sched, int64_t B, int64_t step, int elem_bytes,
                                   const void* send, void* dst, const int64_t* sbase, cudaStream_t st)
 {
-    const unsigned grid = (unsigned)pairs_per_step(sched, t.src.P, B);
+    const dim3 grid = step_grid(pairs_per_step(sched, t.src.P, B));
     if (elem_bytes == 16)
         segment_unpack_kernel<uint4><<<grid, 128, 0, st>>>(t, sched, B, step, (const uint4*)send, (uint4*)dst, sbase);
     else
