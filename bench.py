@@ -766,7 +766,8 @@ def run_reference(args, rank, world):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 2),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": WORKLOAD, "sample": "one forward 256^3 transform per step, P cycling 16/64/256"},
+           "config": {"workload": WORKLOAD, "shape": [n, n, n], "P": list(PS), "transforms_per_step": 6,
+                      "sample": "one forward 256^3 transform per step, P cycling 16/64/256"},
            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": "one forward 256^3 complex128 transform per step (single thread)"},
            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
