@@ -280,3 +280,35 @@ def test_host_exec_and_tuning(torch):
         assert t["fft"]["ms"] > 0
     finally:
         of.openfft_destroy(plan)
+
+
+# --------------------------------------------- the longest supported axes --
+
+@pytest.mark.parametrize("shape,P", [((2048, 2, 3), 2), ((3, 2048, 2), 3), ((2, 3, 2048), 2),
+                                     ((1792, 4, 3), 6), ((5, 1000, 2), 4)])
+@pytest.mark.parametrize("dtype", [of.C2C_F64, of.C2C_F32])
+def test_longest_axes_every_candidate(torch, shape, P, dtype):
+    """Axes at the 2048 limit (and 1792 = 2^8 7, 1000 = 2^3 5^3) on each axis position."""
+    Na, Nb, Nc = shape
+    x = synth.complex_field(shape, seed=Na + 7 * Nb + 31 * Nc)
+    if dtype == of.C2C_F32:
+        x = x.astype(np.complex64)
+    ref = oracle.fft3d(x.astype(np.complex128), Na, Nb, Nc, P, oracle.FORWARD)
+    tol = TOL_F64 if dtype == of.C2C_F64 else TOL_F32
+    plan = of.openfft_plan(Na, Nb, Nc, P, dtype)
+    try:
+        for c in _all_candidates(plan):
+            of.openfft_set_tuning(plan, of.TUNE_USER, c)
+            y = _run(torch, plan, x, of.FORWARD, dtype)
+            assert oracle.rel_l2(y, ref) < tol, (shape, P, of.openfft_candidate(plan, c))
+            z = _run(torch, plan, y.astype(x.dtype), of.BACKWARD, dtype)
+            assert oracle.rel_l2(z, x.reshape(-1).astype(np.complex128)) < 2 * tol
+    finally:
+        of.openfft_destroy(plan)
+
+
+def test_axes_beyond_the_limit_are_refused(torch):
+    for shape in [(4096, 2, 2), (2, 2, 4096), (2, 2049, 2), (2, 2, 2 * 11 * 13)]:
+        with pytest.raises(of.OpenFFTError) as ei:
+            of.openfft_plan(*shape, 2, of.C2C_F64)
+        assert ei.value.status == of.ERR_UNSUPPORTED_RADIX, shape

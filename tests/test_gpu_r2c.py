@@ -55,7 +55,7 @@ def _c2r(torch, plan, h, dtype, N):
 
 
 SHAPES = [((32, 32, 32), 4), ((120, 144, 160), 32), ((12, 10, 15), 6), ((64, 48, 256), 64),
-          ((16, 20, 24), 200), ((9, 7, 2), 14), ((40, 36, 1), 8)]
+          ((16, 20, 24), 200), ((9, 7, 2), 14), ((40, 36, 1), 8), ((3, 2, 2048), 3), ((2, 5, 1792), 4)]
 
 
 @pytest.mark.parametrize("dtype", [of.R2C_F64, of.R2C_F32])
