@@ -16,12 +16,16 @@
 //   parts of V1 and V2 only.  Re and Im of DFT(Z), times the scale, are the
 //   two real lines.
 //
-// One CTA per tile of 2G real lines (G complex lines) in two ping-pong
-// [n][G + 1] shared-memory tiles; the radix passes are those of the generic
-// stage kernel (any supported n, runtime radix plan).
+// Power-of-two n (32..512): one warp per complex line (a pair of real lines)
+// in the padded per-warp layout of the warp-per-line stage kernel, with its
+// radix passes; persistent CTAs of 8 warps.  Other n: one CTA per tile of 2G
+// real lines (G complex lines) in two ping-pong [n][G + 1] shared-memory
+// tiles, with the radix passes of the generic stage kernel (any supported n,
+// runtime radix plan).
 #include <cuda_runtime.h>
 
 #include "fft_stage.h"
+#include "fft_warp.cuh"
 #include "generic_stage.cuh"
 #include "stage_io.cuh"
 
@@ -180,9 +184,138 @@ __global__ void __launch_bounds__(kStageThreads) c2r_stage_kernel(const StageArg
     }
 }
 
+// ------------------------------------------- warp per pair of real lines --
+
+constexpr int kRealWarpG = 8;       // complex lines (warps) per CTA
+
+// Forward real stage, power-of-two N: warp w of tile t takes real lines
+// l0 + 2w and l0 + 2w + 1 (l0 = 2 G t); the CTA then separates the spectra of
+// its 2G lines and stores frequency k of all of them (2G consecutive
+// elements of the half array) at a time.
+template <class A, int N, int G>
+__global__ void __launch_bounds__(32 * G, warp_min_blocks(32 * G, sizeof(typename A::C)))
+r2c_warp_kernel(const StageArgs p, int64_t ntiles)
+{
+    using C = typename A::C;
+    using RP = RealPair<A>;
+    using T = typename RP::T;
+    constexpr int EB = sizeof(C);
+    constexpr int LS = warp_line_stride<EB>(N);
+    constexpr int TWO = 2 * G, SLOTS = 32 * G / TWO;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tile = reinterpret_cast<C*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const typename A::W* tw = reinterpret_cast<const typename A::W*>(p.tw);
+    const T* x = reinterpret_cast<const T*>(p.in);
+    const int64_t L = p.M1;
+    C* line = tile + warp * LS;
+    const int o = tid % TWO, slot = tid / TWO;          // store phase: line o of the tile
+    const C* oline = tile + (o >> 1) * LS;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t l0 = t * TWO;
+        const int64_t la = l0 + 2 * warp, lb = la + 1;
+#pragma unroll
+        for (int u = 0; u < N / 32; ++u) {
+            const int pos = lane + 32 * u;
+            const T a = la < L ? x[la * N + pos] : T(0);
+            const T b = lb < L ? x[lb * N + pos] : T(0);
+            line[wpad<EB>(pos)] = RP::make(a, b);
+        }
+        __syncwarp();
+        WarpLine<A, N>::template passes<0>(line, tw, lane);
+        __syncthreads();                                 // every line of the tile is transformed
+        const int64_t l = l0 + o;
+        if (l < L) {
+            for (int k = slot; k <= N / 2; k += SLOTS) {
+                const C z = oline[wpad<EB>(k)];
+                const C zr = A::conj(oline[wpad<EB>(k == 0 ? 0 : N - k)]);
+                const C X = A::scale((o & 1) ? A::mul_mi(A::sub(z, zr)) : A::add(z, zr), 0.5);
+                Io<A>::store(p.out, p.out_fmt, (int64_t)k * p.Sk + l * p.S1, X);
+            }
+        }
+        __syncthreads();                                 // the tile buffer is free again
+    }
+}
+
+// Inverse real stage, power-of-two N: warp w of tile t extends half lines
+// l0 + 2w and l0 + 2w + 1, transforms, and writes the two real lines.
+template <class A, int N, int G>
+__global__ void __launch_bounds__(32 * G, warp_min_blocks(32 * G, sizeof(typename A::C)))
+c2r_warp_kernel(const StageArgs p, int64_t ntiles)
+{
+    using C = typename A::C;
+    using RP = RealPair<A>;
+    using T = typename RP::T;
+    constexpr int EB = sizeof(C);
+    constexpr int LS = warp_line_stride<EB>(N);
+    constexpr int NH = N / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tile = reinterpret_cast<C*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const typename A::W* tw = reinterpret_cast<const typename A::W*>(p.tw);
+    T* y = reinterpret_cast<T*>(p.out);
+    const int64_t L = p.M1;
+    C* line = tile + warp * LS;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t la = t * 2 * G + 2 * warp, lb = la + 1;
+        for (int k = lane; k < NH; k += 32) {
+            const C v1 = la < L ? Io<A>::load(p.in, p.in_fmt, la * NH + k) : A::zero();
+            const C v2 = lb < L ? Io<A>::load(p.in, p.in_fmt, lb * NH + k) : A::zero();
+            if (k == 0 || 2 * k == N) {
+                line[wpad<EB>(k)] = RP::re_parts(v1, v2);
+            } else {
+                line[wpad<EB>(k)] = A::add(v1, mul_i<A>(v2));
+                line[wpad<EB>(N - k)] = A::add(A::conj(v1), mul_i<A>(A::conj(v2)));
+            }
+        }
+        __syncwarp();
+        WarpLine<A, N>::template passes<0>(line, tw, lane);
+#pragma unroll
+        for (int u = 0; u < N / 32; ++u) {
+            const int pos = lane + 32 * u;
+            const C z = line[wpad<EB>(pos)];
+            if (la < L) y[la * N + pos] = (T)RP::part(z, 0, p.scale);
+            if (lb < L) y[lb * N + pos] = (T)RP::part(z, 1, p.scale);
+        }
+        __syncwarp();                                    // the line is free again
+    }
+}
+
+template <class A, int N>
+cudaError_t launch_real_warp(const StageLaunch& L, cudaStream_t st)
+{
+    constexpr int G = kRealWarpG;
+    const size_t smem = (size_t)G * warp_line_stride<sizeof(typename A::C)>(N) * sizeof(typename A::C);
+    static int per_sm_r2c = -1, per_sm_c2r = -1;
+    const bool fwd = L.family == KERNEL_R2C;
+    int& per_sm = fwd ? per_sm_r2c : per_sm_c2r;
+    if (per_sm < 0) {
+        int b = 0;
+        cudaError_t e = fwd ? persistent_ctas_per_sm((const void*)r2c_warp_kernel<A, N, G>, 32 * G, smem, &b)
+                            : persistent_ctas_per_sm((const void*)c2r_warp_kernel<A, N, G>, 32 * G, smem, &b);
+        if (e) return e;
+        per_sm = b;
+    }
+    const int64_t ntiles = (L.args.M1 + 2 * G - 1) / (2 * G);
+    int64_t grid = (int64_t)L.sms * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    if (grid < 1) grid = 1;
+    if (fwd) r2c_warp_kernel<A, N, G><<<(unsigned)grid, 32 * G, smem, st>>>(L.args, ntiles);
+    else c2r_warp_kernel<A, N, G><<<(unsigned)grid, 32 * G, smem, st>>>(L.args, ntiles);
+    return cudaGetLastError();
+}
+
 template <class A>
 cudaError_t launch_real_a(const StageLaunch& L, cudaStream_t st)
 {
+    switch (L.args.n) {
+    case 32: return launch_real_warp<A, 32>(L, st);
+    case 64: return launch_real_warp<A, 64>(L, st);
+    case 128: return launch_real_warp<A, 128>(L, st);
+    case 256: return launch_real_warp<A, 256>(L, st);
+    case 512: return launch_real_warp<A, 512>(L, st);
+    default: break;
+    }
     static bool attr_r2c = false, attr_c2r = false;
     const unsigned grid = (unsigned)L.grid;
     if (L.family == KERNEL_R2C) {
