@@ -333,6 +333,15 @@ int openfft_exec_many(openfft_plan_t plan, const void* const* in, void* const* o
  * that their wait runs out (value = 0 undoes it). */
 int openfft_batch_debug(openfft_plan_t plan, int what, long long value);
 
+/* Test controls of the tensor-core DFT-GEMM stages (OPENFFT_C2C_SPLIT_* plans),
+ * process-wide: what = 1 sets the budget of their bounded MMA completion
+ * waits to `value` clock cycles (value <= 0: the default, about one second);
+ * what = 2 with value != 0 makes the stages issue and commit no MMAs, so that
+ * every completion wait runs out: the kernel stores OPENFFT_ERR_TIMEOUT, frees
+ * its tensor memory and returns, and openfft_sync reports the status
+ * (value = 0 undoes it).  Nothing is in flight when a wait runs out. */
+int openfft_tc_debug(int what, long long value);
+
 /* ------------------------------------------------- allocation-free ----- */
 
 /* The same transform as openfft_exec_c2c (fused variant, default arithmetic

@@ -18,6 +18,7 @@
 
 #include "../../include/openfft_gb.h"
 #include "decomp.h"
+#include "dftgemm.h"
 #include "fft_stage.h"
 #include "redistribute.h"
 #include "batch.h"
@@ -999,6 +1000,14 @@ int openfft_batch_debug(openfft_plan_t plan, int what, long long value)
         return OPENFFT_OK;
     }
     return fail(OPENFFT_ERR_INVALID_ARG, "what must be 1 (wait budget) or 2 (stall injection)");
+}
+
+int openfft_tc_debug(int what, long long value)
+{
+    if (what != 1 && what != 2) return fail(OPENFFT_ERR_INVALID_ARG, "what must be 1 (wait budget) or 2 (skip the MMAs)");
+    cudaError_t e = dftgemm_test_controls(what, value);
+    if (e) return cuda_fail(e, "DFT-GEMM test controls");
+    return OPENFFT_OK;
 }
 
 int openfft_set_timing(openfft_plan_t plan, int enable)

@@ -36,6 +36,7 @@
 #include <algorithm>
 
 #include "../../include/openfft_gb.h"
+#include "dftgemm.h"
 #include "fft_stage.h"
 #include "fft_tile.cuh"
 #include "stage_io.cuh"
@@ -49,6 +50,12 @@ constexpr int kThreads = 256;
 constexpr int kPrefetch = 16;                     // register prefetch: up to 16 elements per thread
 constexpr int kMaxBlocks = 4;                     // 128-row blocks per pass (tensor-memory columns 64 each)
 constexpr long long kWaitBudget = 2000000000LL;   // about one second of clock cycles
+
+// Test controls (process-wide): the completion-wait budget in clock cycles,
+// and a switch that leaves the MMAs of every block unissued and uncommitted so
+// that the bounded completion waits run out (nothing is in flight then).
+__device__ long long g_wait_budget = kWaitBudget;
+__device__ int g_skip_mma = 0;
 
 struct GemmShape {
     int n, R, S, G, Rp, np;
@@ -295,7 +302,7 @@ __device__ __forceinline__ void stage_block(const GemmShape& sh, const float2* l
 template <bool TF32, int PASS>
 __device__ __forceinline__ bool gemm_pass(const GemmShape& sh, float2* lines, unsigned char* smem, const float2* tws,
                                           int conj_in, uint32_t d_tmem, uint64_t* mbar, uint32_t& phases,
-                                          int* status, int* s_abort)
+                                          int* status, int* s_abort, long long budget, int skip_mma)
 {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 127, half = tid >> 7;
     const int K = PASS ? sh.K2 : sh.K1, N = PASS ? sh.N2 : sh.N1;
@@ -310,7 +317,7 @@ __device__ __forceinline__ bool gemm_pass(const GemmShape& sh, float2* lines, un
         tc::fence_smem_to_async();
         tc::fence_before_sync();
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && !skip_mma) {
             tc::fence_after_sync();
             const uint32_t bb = tc::smem_u32(smem + sh.off_b);
             const uint32_t bh = PASS ? bb + sh.b2hi : bb, bl = bb + (PASS ? sh.b2lo : sh.b1lo);
@@ -325,7 +332,7 @@ __device__ __forceinline__ bool gemm_pass(const GemmShape& sh, float2* lines, un
     // take no issue slots from the other CTAs on the SM.
     const int last = nblk - 1;
     if (warp == 0) {
-        bool ok = tc::mbar_wait(&mbar[last], (phases >> last) & 1u, kWaitBudget);
+        bool ok = tc::mbar_wait(&mbar[last], (phases >> last) & 1u, budget);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok && tid == 0) { atomicCAS(status, OPENFFT_OK, OPENFFT_ERR_TIMEOUT); *s_abort = 1; }
     }
@@ -412,6 +419,8 @@ __global__ void __launch_bounds__(kThreads) dftgemm_kernel(const StageArgs p, co
     float2* const tws = reinterpret_cast<float2*>(smem + sh.off_tw);
     const int cnt = (sh.G * sh.n + kThreads - 1) / kThreads;
     const bool prefetch = cnt <= kPrefetch;
+    const long long budget = g_wait_budget;
+    const int skip_mma = g_skip_mma;
 
     // B image and twiddle table -> shared memory
     const char* bsrc = reinterpret_cast<const char*>(p.aux);
@@ -444,8 +453,10 @@ __global__ void __launch_bounds__(kThreads) dftgemm_kernel(const StageArgs p, co
         } else if (next < ntiles) {
             fetch_regs(p, sh, next, r, cnt);          // in flight while this tile runs
         }
-        if (!gemm_pass<TF32, 0>(sh, lines, smem, tws, p.conj_in, d_tmem, mbar, phases, status, &s_abort)) break;
-        if (!gemm_pass<TF32, 1>(sh, lines, smem, tws, 0, d_tmem, mbar, phases, status, &s_abort)) break;
+        if (!gemm_pass<TF32, 0>(sh, lines, smem, tws, p.conj_in, d_tmem, mbar, phases, status, &s_abort, budget,
+                                skip_mma)) break;
+        if (!gemm_pass<TF32, 1>(sh, lines, smem, tws, 0, d_tmem, mbar, phases, status, &s_abort, budget,
+                                skip_mma)) break;
         store_tile(p, sh, tile, lines);
         __syncthreads();                              // every read of this tile's lines is done
         if (prefetch && next < ntiles) {
@@ -494,6 +505,16 @@ GemmShape make_shape(int n, int R, int S, int G, bool tf32)
 }
 
 }  // namespace
+
+cudaError_t dftgemm_test_controls(int what, long long value)
+{
+    if (what == 1) {
+        const long long b = value > 0 ? value : kWaitBudget;
+        return cudaMemcpyToSymbol(g_wait_budget, &b, sizeof(b));
+    }
+    const int v = value != 0;
+    return cudaMemcpyToSymbol(g_skip_mma, &v, sizeof(v));
+}
 
 // Factor n = R S (2 <= R, S <= 32) with the least padded GEMM work.
 bool dftgemm_factor(int n, int tf32, int* R, int* S)

@@ -43,7 +43,7 @@ EXPORTS = [
     "openfft_plan_many", "openfft_exec_many", "openfft_batch_debug",
     "openfft_mlp_num_params", "openfft_mlp_predict", "openfft_mlp_loss_grad", "openfft_mlp_train",
     "openfft_num_features", "openfft_candidate_features", "openfft_tune_times", "openfft_set_cost_model",
-    "openfft_tc_gemm", "openfft_exec_r2c", "openfft_exec_c2r",
+    "openfft_tc_gemm", "openfft_exec_r2c", "openfft_exec_c2r", "openfft_tc_debug",
 ]
 
 _lock = threading.Lock()
@@ -79,6 +79,7 @@ def load():
             "openfft_plan": (vp, [i32, i32, i32, i32, i32]),
             "openfft_exec_c2c": (i32, [vp, vp, vp, i32]),
             "openfft_exec_r2c": (i32, [vp, vp, vp]),
+            "openfft_tc_debug": (i32, [i32, ctypes.c_longlong]),
             "openfft_exec_c2r": (i32, [vp, vp, vp]),
             "openfft_exec_c2c_host": (i32, [vp, vp, vp, i32]),
             "openfft_destroy": (None, [vp]),
@@ -147,6 +148,11 @@ def openfft_plan(Na: int, Nb: int, Nc: int, P: int, dtype: int) -> int:
 
 def openfft_exec_c2c(plan: int, inp, out, direction: int) -> None:
     _check(load().openfft_exec_c2c(plan, _ptr(inp), _ptr(out), direction))
+
+
+def openfft_tc_debug(what: int, value: int) -> None:
+    """Test controls of the DFT-GEMM stages: 1 = wait budget (cycles), 2 = skip the MMAs."""
+    _check(load().openfft_tc_debug(what, value))
 
 
 def openfft_exec_r2c(plan: int, inp, out) -> None:

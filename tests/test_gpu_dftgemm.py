@@ -70,3 +70,33 @@ def test_dftgemm_rejects_unfactorable_axes(torch):
         with pytest.raises(of.OpenFFTError) as ei:
             of.openfft_plan(*shape, 2, of.C2C_SPLIT_TF32)
         assert ei.value.status == of.ERR_UNSUPPORTED_RADIX
+
+
+def test_dftgemm_wait_timeout_is_reported(torch):
+    """A completion wait that runs out (no MMA issued: nothing in flight) is
+    reported as OPENFFT_ERR_TIMEOUT, and the context stays usable."""
+    Na = Nb = Nc = 32
+    x = synth.complex_field((Na, Nb, Nc), seed=synth.config_seed(3)).astype(np.complex64)
+    ref = oracle.fft3d(x.astype(np.complex128), Na, Nb, Nc, 4, oracle.FORWARD)
+    plan = of.openfft_plan(Na, Nb, Nc, 4, of.C2C_SPLIT_TF32)
+    try:
+        xd = torch.from_numpy(x.reshape(-1)).to("cuda")
+        yd = torch.empty_like(xd)
+        of.openfft_set_stream(plan, torch.cuda.current_stream())
+        try:
+            of.openfft_tc_debug(1, 2_000_000)            # about 1 ms of clock cycles
+            of.openfft_tc_debug(2, 1)                    # no MMA is issued or committed
+            of.openfft_exec_c2c(plan, xd, yd, of.FORWARD)
+            with pytest.raises(of.OpenFFTError) as ei:
+                of.openfft_sync(plan)
+            assert ei.value.status == of.ERR_TIMEOUT
+        finally:
+            of.openfft_tc_debug(2, 0)
+            of.openfft_tc_debug(1, 0)
+        y = _run(torch, plan, x, of.FORWARD)
+        assert oracle.rel_l2(y, ref) < 1e-5
+    finally:
+        of.openfft_destroy(plan)
+    with pytest.raises(of.OpenFFTError) as ei:
+        of.openfft_tc_debug(3, 0)
+    assert ei.value.status == of.ERR_INVALID_ARG
