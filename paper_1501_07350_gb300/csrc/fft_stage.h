@@ -61,6 +61,16 @@ cudaError_t stage_kernels_init(int max_dyn_smem);
 // (shared memory with the whole carveout as shared memory, registers,
 // threads); sets the kernel's dynamic shared memory limit and carveout.
 cudaError_t persistent_ctas_per_sm(const void* func, int threads, size_t dyn_smem, int* per_sm);
+// Launch properties are cached per device (kernel attributes are per device):
+// the current device's slot of `slots`, or nullptr beyond kMaxDevices (then
+// the caller recomputes on every launch).
+constexpr int kMaxDevices = 64;
+inline int* device_slot(int (&slots)[kMaxDevices])
+{
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) return nullptr;
+    return &slots[d];
+}
 // specialised kernels (fft_tile_*.cu); *handled = false when (n, G) has none
 cudaError_t launch_tile_f64(const StageLaunch& L, cudaStream_t st, bool* handled);
 cudaError_t launch_tile_f32(const StageLaunch& L, cudaStream_t st, bool* handled);

@@ -310,12 +310,13 @@ cudaError_t launch_tile_n(const StageLaunch& L, cudaStream_t st)
     constexpr int T = tile_threads(N, G);
     using TL = Tile<A, N, G, T>;
     const size_t smem = 2 * (size_t)TL::kElems * sizeof(typename A::C);
-    static int blocks_per_sm = -1;
-    if (blocks_per_sm < 0) {
-        int b = 0;
-        cudaError_t e = persistent_ctas_per_sm((const void*)fft_tile_kernel<A, N, G, T>, T, smem, &b);
+    static int cached[kMaxDevices] = {};          // CTAs per SM on each device, 0 = not yet known
+    int* slot = device_slot(cached);
+    int blocks_per_sm = slot ? *slot : 0;
+    if (blocks_per_sm == 0) {
+        cudaError_t e = persistent_ctas_per_sm((const void*)fft_tile_kernel<A, N, G, T>, T, smem, &blocks_per_sm);
         if (e) return e;
-        blocks_per_sm = b;
+        if (slot) *slot = blocks_per_sm;
     }
     const int64_t ntiles = L.grid;
     int64_t grid = (int64_t)L.sms * blocks_per_sm;

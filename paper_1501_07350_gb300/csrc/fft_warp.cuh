@@ -247,12 +247,13 @@ cudaError_t launch_warp_n(const StageLaunch& L, cudaStream_t st)
     constexpr int T = 32 * G;
     const size_t smem = (warp_double_buffer<A, N>() ? 2 : 1) * (size_t)G * warp_line_stride<sizeof(typename A::C)>(N) *
                         sizeof(typename A::C);
-    static int blocks_per_sm = -1;
-    if (blocks_per_sm < 0) {
-        int b = 0;
-        cudaError_t e = persistent_ctas_per_sm((const void*)fft_warp_kernel<A, N, G>, T, smem, &b);
+    static int cached[kMaxDevices] = {};          // CTAs per SM on each device, 0 = not yet known
+    int* slot = device_slot(cached);
+    int blocks_per_sm = slot ? *slot : 0;
+    if (blocks_per_sm == 0) {
+        cudaError_t e = persistent_ctas_per_sm((const void*)fft_warp_kernel<A, N, G>, T, smem, &blocks_per_sm);
         if (e) return e;
-        blocks_per_sm = b;
+        if (slot) *slot = blocks_per_sm;
     }
     const int64_t ntiles = L.grid;
     int64_t grid = (int64_t)L.sms * blocks_per_sm;

@@ -286,15 +286,15 @@ cudaError_t launch_real_warp(const StageLaunch& L, cudaStream_t st)
 {
     constexpr int G = kRealWarpG;
     const size_t smem = (size_t)G * warp_line_stride<sizeof(typename A::C)>(N) * sizeof(typename A::C);
-    static int per_sm_r2c = -1, per_sm_c2r = -1;
+    static int cached_r2c[kMaxDevices] = {}, cached_c2r[kMaxDevices] = {};   // CTAs per SM, 0 = unknown
     const bool fwd = L.family == KERNEL_R2C;
-    int& per_sm = fwd ? per_sm_r2c : per_sm_c2r;
-    if (per_sm < 0) {
-        int b = 0;
-        cudaError_t e = fwd ? persistent_ctas_per_sm((const void*)r2c_warp_kernel<A, N, G>, 32 * G, smem, &b)
-                            : persistent_ctas_per_sm((const void*)c2r_warp_kernel<A, N, G>, 32 * G, smem, &b);
+    int* slot = device_slot(fwd ? cached_r2c : cached_c2r);
+    int per_sm = slot ? *slot : 0;
+    if (per_sm == 0) {
+        cudaError_t e = fwd ? persistent_ctas_per_sm((const void*)r2c_warp_kernel<A, N, G>, 32 * G, smem, &per_sm)
+                            : persistent_ctas_per_sm((const void*)c2r_warp_kernel<A, N, G>, 32 * G, smem, &per_sm);
         if (e) return e;
-        per_sm = b;
+        if (slot) *slot = per_sm;
     }
     const int64_t ntiles = (L.args.M1 + 2 * G - 1) / (2 * G);
     int64_t grid = (int64_t)L.sms * per_sm;
@@ -316,22 +316,24 @@ cudaError_t launch_real_a(const StageLaunch& L, cudaStream_t st)
     case 512: return launch_real_warp<A, 512>(L, st);
     default: break;
     }
-    static bool attr_r2c = false, attr_c2r = false;
+    static int attr_r2c[kMaxDevices] = {}, attr_c2r[kMaxDevices] = {};     // attribute set on that device
     const unsigned grid = (unsigned)L.grid;
     if (L.family == KERNEL_R2C) {
-        if (!attr_r2c) {
+        int* slot = device_slot(attr_r2c);
+        if (!slot || !*slot) {
             cudaError_t e = cudaFuncSetAttribute(r2c_stage_kernel<A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  200 * 1024);
             if (e) return e;
-            attr_r2c = true;
+            if (slot) *slot = 1;
         }
         r2c_stage_kernel<A><<<grid, kStageThreads, L.smem, st>>>(L.args);
     } else {
-        if (!attr_c2r) {
+        int* slot = device_slot(attr_c2r);
+        if (!slot || !*slot) {
             cudaError_t e = cudaFuncSetAttribute(c2r_stage_kernel<A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  200 * 1024);
             if (e) return e;
-            attr_c2r = true;
+            if (slot) *slot = 1;
         }
         c2r_stage_kernel<A><<<grid, kStageThreads, L.smem, st>>>(L.args);
     }
