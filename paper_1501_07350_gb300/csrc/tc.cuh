@@ -153,12 +153,13 @@ __host__ __device__ __forceinline__ uint32_t op_offset(int row, int k, int KT, i
     return (uint32_t)(((row >> 3) * KT + (k / per16)) * 128 + (row & 7) * 16 + (k % per16) * esize);
 }
 
-// Split x into hi + lo: tf32 keeps 10 fraction bits (round to nearest), bf16 7.
+// x rounded to tf32 (10 fraction bits; to nearest, ties away from zero): one
+// conversion instruction, the low 13 bits of the result are zero.
 __device__ __forceinline__ float round_tf32(float x)
 {
-    uint32_t b = __float_as_uint(x);
-    b = (b + 0x1000u) & 0xFFFFE000u;          // round half up on the 13 dropped bits
-    return __uint_as_float(b);
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
 }
 
 }  // namespace tc
