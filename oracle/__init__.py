@@ -39,36 +39,40 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def _configure(lib):
+    """Argument and result types of the library's entry points."""
+    i64, i32, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
+    p64 = ctypes.POINTER(ctypes.c_int64)
+    lib.oracle_f.restype = i64
+    lib.oracle_f.argtypes = [i64] * 5
+    lib.oracle_boundaries.restype = i32
+    lib.oracle_boundaries.argtypes = [i64] * 4 + [p64]
+    lib.oracle_box.restype = i32
+    lib.oracle_box.argtypes = [i64] * 5 + [p64, p64, p64, p64]
+    lib.oracle_degree.restype = i32
+    lib.oracle_degree.argtypes = [i64] * 3
+    lib.oracle_fft1d.restype = None
+    lib.oracle_fft1d.argtypes = [i64, vp, vp, i32]
+    lib.oracle_dft1d_brute.restype = None
+    lib.oracle_dft1d_brute.argtypes = [i64, vp, vp, i32]
+    lib.oracle_dft3d_brute.restype = None
+    lib.oracle_dft3d_brute.argtypes = [i64, i64, i64, vp, vp, i32]
+    lib.oracle_dft3d_line.restype = None
+    lib.oracle_dft3d_line.argtypes = [i64, i64, i64, vp, i32, i64, i64, vp]
+    lib.oracle_redistribute.restype = i32
+    lib.oracle_redistribute.argtypes = [i64] * 4 + [i32, vp, vp, vp]
+    lib.oracle_fft3d.restype = i32
+    lib.oracle_fft3d.argtypes = [i64] * 4 + [i32, vp, vp, vp, vp]
+    lib.oracle_rfft3d.restype = i32
+    lib.oracle_rfft3d.argtypes = [i64] * 4 + [i32, vp, vp, vp, vp]
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            i64, i32, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
-            p64 = ctypes.POINTER(ctypes.c_int64)
-            lib.oracle_f.restype = i64
-            lib.oracle_f.argtypes = [i64] * 5
-            lib.oracle_boundaries.restype = i32
-            lib.oracle_boundaries.argtypes = [i64] * 4 + [p64]
-            lib.oracle_box.restype = i32
-            lib.oracle_box.argtypes = [i64] * 5 + [p64, p64, p64, p64]
-            lib.oracle_degree.restype = i32
-            lib.oracle_degree.argtypes = [i64] * 3
-            lib.oracle_fft1d.restype = None
-            lib.oracle_fft1d.argtypes = [i64, vp, vp, i32]
-            lib.oracle_dft1d_brute.restype = None
-            lib.oracle_dft1d_brute.argtypes = [i64, vp, vp, i32]
-            lib.oracle_dft3d_brute.restype = None
-            lib.oracle_dft3d_brute.argtypes = [i64, i64, i64, vp, vp, i32]
-            lib.oracle_dft3d_line.restype = None
-            lib.oracle_dft3d_line.argtypes = [i64, i64, i64, vp, i32, i64, i64, vp]
-            lib.oracle_redistribute.restype = i32
-            lib.oracle_redistribute.argtypes = [i64] * 4 + [i32, vp, vp, vp]
-            lib.oracle_fft3d.restype = i32
-            lib.oracle_fft3d.argtypes = [i64] * 4 + [i32, vp, vp, vp, vp]
-            lib.oracle_rfft3d.restype = i32
-            lib.oracle_rfft3d.argtypes = [i64] * 4 + [i32, vp, vp, vp, vp]
-            _lib = lib
+            _lib = _configure(ctypes.CDLL(build()))
     return _lib
 
 
