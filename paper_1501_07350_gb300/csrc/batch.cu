@@ -1,7 +1,7 @@
 // batch.cu -- many 3-D transforms of uneven sizes in one persistent launch,
 // replayed from a captured CUDA graph.
 //
-// Work items are runs of up to kTilesPerItem tiles (of G lines each) of one
+// Work items are runs of up to kTilesPerItem (16) tiles (of G lines each) of one
 // stage of one transform, handed out
 // in stage-major order (every stage-1 tile of every transform, then every
 // stage-2 tile, then every stage-3 tile) through one atomic queue head.  A
@@ -32,7 +32,8 @@
 namespace ofg {
 
 constexpr int kBatchThreads = 256;
-constexpr int kTilesPerItem = 4;           // tiles of one (stage, transform) per work item
+constexpr int kTilesPerItem = 16;          // tiles of one (stage, transform) per work item (the
+                                           // queue and dependency work of an item is serial)
 
 struct BatchCounters {
     unsigned long long next;   // queue head
