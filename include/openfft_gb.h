@@ -161,10 +161,23 @@ int openfft_exec_r2c(openfft_plan_t plan, const void* in, void* out);
 int openfft_exec_c2r(openfft_plan_t plan, const void* in, void* out);
 
 /* Same transform with HOST buffers: copies `host_in` to plan-owned device
- * memory, executes, copies the result to `host_out` and waits.  Page-locked
- * host memory gives the fastest copies.  The plan allocates its two device
- * staging arrays on the first call. */
+ * memory, executes, copies the result to `host_out` and waits (complex
+ * plans only; N elements of the plan's external type each way).  The copies
+ * run on a plan-owned second stream in ranges of lines, so that the first
+ * stage starts on each range of the input as soon as it has arrived and each
+ * range of the last stage's output is copied back as soon as it is written
+ * (the host link, not the transform, bounds this call).  The result is bit
+ * for bit that of openfft_exec_c2c.  Page-locked host memory gives the
+ * fastest copies; `host_in` may equal `host_out`.  The plan allocates its
+ * two device staging arrays, the stream and its events on the first call.
+ * While the phase timer is on (openfft_set_timing) the copies bracket the
+ * whole transform instead. */
 int openfft_exec_c2c_host(openfft_plan_t plan, const void* host_in, void* host_out, int dir);
+
+/* Number of line ranges of openfft_exec_c2c_host: 1 (no overlap) to 32;
+ * 0 (the default) takes one per 8 MiB of the array, 1 to 16.  INVALID_ARG
+ * outside 0..32. */
+int openfft_set_host_chunks(openfft_plan_t plan, int chunks);
 
 /* Finalisation phase: frees everything the plan owns.  NULL-safe. */
 void openfft_destroy(openfft_plan_t plan);

@@ -96,6 +96,10 @@ struct TransposeTables {
 
 }  // namespace
 
+// Host-buffer execution overlaps the host<->device copies with the line-local
+// first and last stages in at most this many line ranges.
+constexpr int kMaxHostChunks = 32;
+
 struct openfft_plan_s {
     int Na, Nb, Nc, P, dtype;
     int64_t N;
@@ -112,6 +116,9 @@ struct openfft_plan_s {
     std::vector<Op> ops_fwd, ops_bwd;
     void* stage_in = nullptr;     // host-exec staging (lazy)
     void* stage_out = nullptr;
+    cudaStream_t copy_stream = nullptr;            // host-exec copies (lazy)
+    cudaEvent_t host_ev[2 * kMaxHostChunks + 1] = {};
+    int host_chunks = 0;                           // 0 = chosen by size
     // execution-time breakdown
     bool timing = false;
     std::vector<cudaEvent_t> ev;  // pool
@@ -419,15 +426,19 @@ int record(openfft_plan_s* p, int cat)
     return OPENFFT_OK;
 }
 
-int run_ops(openfft_plan_s* p, const std::vector<Op>& ops, const void* in, void* out, int arith)
+// Runs ops[i0, i1) on the plan's stream (the whole list by default).
+int run_ops(openfft_plan_s* p, const std::vector<Op>& ops, const void* in, void* out, int arith,
+            size_t i0 = 0, size_t i1 = SIZE_MAX)
 {
     const int E = elem_bytes_of(arith);
+    if (i1 > ops.size()) i1 = ops.size();
     if (p->timing) {
         if (p->ev_used + ops.size() + 1 > p->ev.size()) { int st = fold_timing(p); if (st) return st; }
         int st = record(p, -1);
         if (st) return st;
     }
-    for (const Op& o : ops) {
+    for (size_t i = i0; i < i1; ++i) {
+        const Op& o = ops[i];
         void* s = resolve(p, o.src, in, out);
         void* d = resolve(p, o.dst, in, out);
         cudaError_t e = cudaSuccess;
@@ -486,6 +497,8 @@ void free_plan(openfft_plan_s* p)
         cudaFree(T.d_C); cudaFree(T.d_sdispl); cudaFree(T.d_rdispl);
     }
     cudaFree(p->stage_in); cudaFree(p->stage_out);
+    if (p->copy_stream) { cudaStreamSynchronize(p->copy_stream); cudaStreamDestroy(p->copy_stream); }
+    for (cudaEvent_t e : p->host_ev) if (e) cudaEventDestroy(e);
     cudaFree(p->d_status);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
     if (p->batch) batch_destroy(p->batch);
@@ -811,22 +824,183 @@ int openfft_exec_c2r(openfft_plan_t plan, const void* in, void* out)
     return run_ops(plan, plan->ops_bwd, in, out, c.arith);
 }
 
+namespace {
+
+int fmt_bytes(int fmt)
+{
+    return fmt == FMT_C64 || fmt == FMT_R64 ? 8 : (fmt == FMT_R32 ? 4 : 16);
+}
+
+// A stage launch restricted to the lines whose coordinate u lies in [u0, u1):
+// u = i2 when M2 > 1, else u = i1 (then i2 = 0 and M1 plays no part in the
+// addresses).  The restricted launch reads from in + *in_off and writes to
+// out + *out_off (elements); *lines is its number of lines, which are
+// contiguous in the input.
+StageLaunch stage_lines(const StageLaunch& L, int64_t u0, int64_t u1, int64_t* in_off, int64_t* out_off,
+                        int64_t* lines)
+{
+    StageLaunch c = L;
+    StageArgs& a = c.args;
+    if (a.M2 > 1) {
+        *in_off = u0 * a.M1 * a.n; *out_off = u0 * a.S2; *lines = (u1 - u0) * a.M1;
+        a.M2 = u1 - u0;
+    } else {
+        *in_off = u0 * a.n; *out_off = u0 * a.S1; *lines = u1 - u0;
+        a.M1 = u1 - u0;
+    }
+    const int64_t Mg = a.group_i2 ? a.M2 : a.M1;
+    a.ngroups = (Mg + a.G - 1) / a.G;
+    c.grid = a.ngroups * (a.group_i2 ? a.M1 : a.M2);
+    return c;
+}
+
+// Boundaries of k line ranges of a stage: multiples of G when the split
+// coordinate is the one that tiles group, so tiles stay whole.
+std::vector<int64_t> line_ranges(const StageArgs& a, int k)
+{
+    const int64_t U = a.M2 > 1 ? a.M2 : a.M1;
+    const int64_t q = ((a.M2 > 1) == (a.group_i2 != 0)) ? a.G : 1;
+    std::vector<int64_t> b{0};
+    for (int i = 1; i < k; ++i) {
+        const int64_t u = U * i / k / q * q;
+        if (u > b.back() && u < U) b.push_back(u);
+    }
+    b.push_back(U);
+    return b;
+}
+
+// The first op can start on each range as soon as its input has arrived: a
+// stage reading the user input whose lines cover the whole array.
+bool splits_input(const openfft_plan_s* p, const Op& o)
+{
+    return o.kind == OP_STAGE && o.src == B_IN && o.stage.family != KERNEL_R2C &&
+           o.stage.args.M1 * o.stage.args.M2 * o.stage.args.n == p->N;
+}
+
+// The last op's ranges can leave as soon as they are written: a stage writing
+// the user output line by line (contiguous lines of n elements).
+bool splits_output(const openfft_plan_s* p, const Op& o)
+{
+    const StageArgs& a = o.stage.args;
+    return o.kind == OP_STAGE && o.dst == B_OUT && o.stage.family != KERNEL_C2R && a.contig_store &&
+           a.Sk == 1 && a.S1 == a.n && (a.M2 == 1 || a.S2 == a.M1 * a.n) && a.M1 * a.M2 * a.n == p->N;
+}
+
+int host_ranges(const openfft_plan_s* p, size_t bytes)
+{
+    if (p->host_chunks > 0) return std::min(p->host_chunks, kMaxHostChunks);
+    const size_t per = (size_t)8 << 20;        // ranges of at least 8 MiB
+    return (int)std::max<size_t>(1, std::min<size_t>(16, bytes / per));
+}
+
+}  // namespace
+
+int openfft_set_host_chunks(openfft_plan_t plan, int chunks)
+{
+    if (!plan) return fail(OPENFFT_ERR_INVALID_ARG, "null plan");
+    if (chunks < 0 || chunks > kMaxHostChunks) return fail(OPENFFT_ERR_INVALID_ARG, "chunks must be 0..32");
+    plan->host_chunks = chunks;
+    return OPENFFT_OK;
+}
+
 int openfft_exec_c2c_host(openfft_plan_t plan, const void* host_in, void* host_out, int dir)
 {
     if (!plan || !host_in || !host_out) return fail(OPENFFT_ERR_INVALID_ARG, "null plan or buffer");
+    if (plan->batch) return fail(OPENFFT_ERR_INVALID_ARG, "batched plan: use openfft_exec_many");
+    if (plan->real) return fail(OPENFFT_ERR_INVALID_ARG, "real plan: use openfft_exec_r2c / openfft_exec_c2r");
+    if (dir != OPENFFT_FORWARD && dir != OPENFFT_BACKWARD) return fail(OPENFFT_ERR_INVALID_ARG, "dir must be -1 or +1");
     const size_t bytes = (size_t)plan->N * plan->elem_bytes;
     if (!plan->stage_in) {
         if (cudaMalloc(&plan->stage_in, bytes) || cudaMalloc(&plan->stage_out, bytes)) {
             cudaGetLastError();
+            cudaFree(plan->stage_in); plan->stage_in = nullptr;
             return fail(OPENFFT_ERR_NOMEM, "staging allocation failed");
         }
     }
+    const std::vector<Op>& ops = dir == OPENFFT_FORWARD ? plan->ops_fwd : plan->ops_bwd;
+    const int arith = plan->cands[(size_t)plan->current].arith;
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(plan->stage_in, host_in, bytes, cudaMemcpyHostToDevice, plan->stream))) return cuda_fail(e, "H2D");
-    int st = openfft_exec_c2c(plan, plan->stage_in, plan->stage_out, dir);
-    if (st) return st;
-    if ((e = cudaMemcpyAsync(host_out, plan->stage_out, bytes, cudaMemcpyDeviceToHost, plan->stream))) return cuda_fail(e, "D2H");
-    if ((e = cudaStreamSynchronize(plan->stream))) return cuda_fail(e, "sync");
+    if (plan->timing || ops.size() < 3) {
+        // one copy each way around the whole transform (the phase timer
+        // brackets whole ops)
+        if ((e = cudaMemcpyAsync(plan->stage_in, host_in, bytes, cudaMemcpyHostToDevice, plan->stream))) return cuda_fail(e, "H2D");
+        int st = run_ops(plan, ops, plan->stage_in, plan->stage_out, arith);
+        if (st) return st;
+        if ((e = cudaMemcpyAsync(host_out, plan->stage_out, bytes, cudaMemcpyDeviceToHost, plan->stream))) return cuda_fail(e, "D2H");
+        if ((e = cudaStreamSynchronize(plan->stream))) return cuda_fail(e, "sync");
+        return OPENFFT_OK;
+    }
+    // Copies run on a second stream, range by range: the first stage starts
+    // on each range of lines as soon as it has arrived, and each range of the
+    // last stage's output leaves as soon as it is written.
+    if (!plan->copy_stream) {
+        if ((e = cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking))) return cuda_fail(e, "copy stream");
+        for (cudaEvent_t& ev : plan->host_ev)
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming))) return cuda_fail(e, "copy events");
+    }
+    cudaStream_t st = plan->stream, cs = plan->copy_stream;
+    cudaEvent_t* ev_in = plan->host_ev + 1;
+    cudaEvent_t* ev_out = plan->host_ev + 1 + kMaxHostChunks;
+    const int k = host_ranges(plan, bytes);
+    const char* hin = static_cast<const char*>(host_in);
+    char* hout = static_cast<char*>(host_out);
+    char* din = static_cast<char*>(plan->stage_in);
+    char* dout = static_cast<char*>(plan->stage_out);
+    // the copies into the staging array wait for work already queued on the plan's stream
+    if ((e = cudaEventRecord(plan->host_ev[0], st)) || (e = cudaStreamWaitEvent(cs, plan->host_ev[0], 0))) return cuda_fail(e, "copy order");
+    const Op& first = ops.front();
+    const Op& last = ops.back();
+    size_t i0 = 0, i1 = ops.size();
+    if (splits_input(plan, first)) {
+        const StageArgs& a = first.stage.args;
+        const std::vector<int64_t> b = line_ranges(a, k);
+        const int Ein = fmt_bytes(a.in_fmt), Eout = fmt_bytes(a.out_fmt);
+        for (size_t j = 0; j + 1 < b.size(); ++j) {
+            int64_t io, oo, lines;
+            stage_lines(first.stage, b[j], b[j + 1], &io, &oo, &lines);
+            if ((e = cudaMemcpyAsync(din + io * Ein, hin + io * Ein, (size_t)(lines * a.n * Ein), cudaMemcpyHostToDevice, cs)) ||
+                (e = cudaEventRecord(ev_in[j], cs)))
+                return cuda_fail(e, "H2D");
+        }
+        char* d = static_cast<char*>(resolve(plan, first.dst, din, dout));
+        for (size_t j = 0; j + 1 < b.size(); ++j) {
+            int64_t io, oo, lines;
+            StageLaunch L = stage_lines(first.stage, b[j], b[j + 1], &io, &oo, &lines);
+            L.args.in = din + io * Ein;
+            L.args.out = d + oo * Eout;
+            if ((e = cudaStreamWaitEvent(st, ev_in[j], 0)) || (e = launch_stage(L, st))) return cuda_fail(e, "first stage");
+        }
+        i0 = 1;
+    } else {
+        if ((e = cudaMemcpyAsync(din, hin, bytes, cudaMemcpyHostToDevice, cs)) || (e = cudaEventRecord(ev_in[0], cs)) ||
+            (e = cudaStreamWaitEvent(st, ev_in[0], 0)))
+            return cuda_fail(e, "H2D");
+    }
+    const bool split_out = splits_output(plan, last);
+    if (split_out) i1 = ops.size() - 1;
+    int status = run_ops(plan, ops, din, dout, arith, i0, i1);
+    if (status) return status;
+    if (split_out) {
+        const StageArgs& a = last.stage.args;
+        const std::vector<int64_t> b = line_ranges(a, k);
+        const int Ein = fmt_bytes(a.in_fmt), Eout = fmt_bytes(a.out_fmt);
+        const char* s = static_cast<const char*>(resolve(plan, last.src, din, dout));
+        for (size_t j = 0; j + 1 < b.size(); ++j) {
+            int64_t io, oo, lines;
+            StageLaunch L = stage_lines(last.stage, b[j], b[j + 1], &io, &oo, &lines);
+            L.args.in = s + io * Ein;
+            L.args.out = dout + oo * Eout;
+            if ((e = launch_stage(L, st)) || (e = cudaEventRecord(ev_out[j], st)) || (e = cudaStreamWaitEvent(cs, ev_out[j], 0)) ||
+                (e = cudaMemcpyAsync(hout + oo * Eout, dout + oo * Eout, (size_t)(lines * a.n * Eout), cudaMemcpyDeviceToHost, cs)))
+                return cuda_fail(e, "last stage");
+        }
+    } else {
+        if ((e = cudaEventRecord(ev_out[0], st)) || (e = cudaStreamWaitEvent(cs, ev_out[0], 0)) ||
+            (e = cudaMemcpyAsync(hout, dout, bytes, cudaMemcpyDeviceToHost, cs)))
+            return cuda_fail(e, "D2H");
+    }
+    if ((e = cudaStreamSynchronize(cs))) return cuda_fail(e, "sync");
+    if ((e = cudaStreamSynchronize(st))) return cuda_fail(e, "sync");
     return OPENFFT_OK;
 }
 

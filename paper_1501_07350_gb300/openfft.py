@@ -43,7 +43,7 @@ EXPORTS = [
     "openfft_plan_many", "openfft_exec_many", "openfft_batch_debug",
     "openfft_mlp_num_params", "openfft_mlp_predict", "openfft_mlp_loss_grad", "openfft_mlp_train",
     "openfft_num_features", "openfft_candidate_features", "openfft_tune_times", "openfft_set_cost_model",
-    "openfft_tc_gemm", "openfft_exec_r2c", "openfft_exec_c2r", "openfft_tc_debug",
+    "openfft_tc_gemm", "openfft_exec_r2c", "openfft_exec_c2r", "openfft_tc_debug", "openfft_set_host_chunks",
 ]
 
 _lock = threading.Lock()
@@ -82,6 +82,7 @@ def load():
             "openfft_tc_debug": (i32, [i32, ctypes.c_longlong]),
             "openfft_exec_c2r": (i32, [vp, vp, vp]),
             "openfft_exec_c2c_host": (i32, [vp, vp, vp, i32]),
+            "openfft_set_host_chunks": (i32, [vp, i32]),
             "openfft_destroy": (None, [vp]),
             "openfft_sync": (i32, [vp]),
             "openfft_set_stream": (i32, [vp, vp]),
@@ -167,6 +168,11 @@ def openfft_exec_c2r(plan: int, inp, out) -> None:
 
 def openfft_exec_c2c_host(plan: int, host_in: np.ndarray, host_out: np.ndarray, direction: int) -> None:
     _check(load().openfft_exec_c2c_host(plan, host_in.ctypes.data, host_out.ctypes.data, direction))
+
+
+def openfft_set_host_chunks(plan: int, chunks: int) -> None:
+    """Line ranges of the host-buffer exec's copy / compute overlap (0 = by size, 1..32)."""
+    _check(load().openfft_set_host_chunks(plan, chunks))
 
 
 def openfft_destroy(plan: int) -> None:
