@@ -241,6 +241,55 @@ def test_double_float_range(torch, scale):
         of.openfft_destroy(plan)
 
 
+def _df_candidates(plan):
+    return [c for c in _all_candidates(plan) if of.openfft_candidate(plan, c)["arith"] == of.ARITH_DOUBLE_FLOAT]
+
+
+@pytest.mark.parametrize("k", [-40, 40])
+def test_double_float_power_of_two_scaling_is_exact(torch, k):
+    """Every double-float operation commutes with scaling by 2^k while no hi or lo
+    part leaves the float range, so the outputs for 2^k x are exactly 2^k times
+    those for x: a bit-exact check of the exponent handling of the double ->
+    double-float split and the join back, both directions."""
+    Na, Nb, Nc, P = 20, 36, 32, 5
+    x = synth.complex_field((Na, Nb, Nc), seed=17)
+    plan = of.openfft_plan(Na, Nb, Nc, P, of.C2C_F64)
+    try:
+        for c in _df_candidates(plan):
+            of.openfft_set_tuning(plan, of.TUNE_USER, c)
+            for direction in (of.FORWARD, of.BACKWARD):
+                y1 = _run(torch, plan, x, direction, of.C2C_F64)
+                y2 = _run(torch, plan, np.ldexp(x.real, k) + 1j * np.ldexp(x.imag, k), direction, of.C2C_F64)
+                want = np.ldexp(y1.real, k) + 1j * np.ldexp(y1.imag, k)
+                assert np.array_equal(y2, want), (k, direction, of.openfft_candidate(plan, c))
+    finally:
+        of.openfft_destroy(plan)
+
+
+@pytest.mark.parametrize("bad", [float("inf"), float("nan"), 1e300])
+def test_double_float_non_finite_and_out_of_range_inputs(torch, bad):
+    """An infinity, a NaN, or a finite value beyond the float exponent range in the
+    input makes every output of the double-float forms non-finite in its real or
+    its imaginary part (each output depends on every input): never a finite wrong
+    number."""
+    Na, Nb, Nc, P = 12, 10, 16, 4
+    x = synth.complex_field((Na, Nb, Nc), seed=19)
+    x[3, 4, 5] = complex(bad, 0.0)
+    plan = of.openfft_plan(Na, Nb, Nc, P, of.C2C_F64)
+    try:
+        for c in _df_candidates(plan):
+            of.openfft_set_tuning(plan, of.TUNE_USER, c)
+            xd = torch.from_numpy(x.reshape(-1)).cuda()
+            yd = torch.empty_like(xd)
+            of.openfft_set_stream(plan, torch.cuda.current_stream())
+            of.openfft_exec_c2c(plan, xd, yd, of.FORWARD)
+            of.openfft_sync(plan)
+            y = yd.cpu().numpy()
+            assert (~np.isfinite(y.real) | ~np.isfinite(y.imag)).all(), (bad, of.openfft_candidate(plan, c))
+    finally:
+        of.openfft_destroy(plan)
+
+
 # ------------------------------------------------------------ errors ----
 
 def test_argument_errors(torch):
