@@ -63,29 +63,40 @@ struct WarpLine {
     using W = typename A::W;
     static constexpr int kPasses = wplan_len(N);
     static constexpr int EB = sizeof(C);
+    static constexpr int LS = warp_line_stride<EB>(N);
 
-    template <int P>
-    __device__ __forceinline__ static void pass(C* line, const W* __restrict__ tw, int lane)
+    // One radix pass over L lines at line0 + i LS (i < L): lane b of the warp
+    // takes butterfly b of every line, so the L lines share the twiddle loads
+    // and give each thread L independent butterflies.
+    template <int P, int L>
+    __device__ __forceinline__ static void pass(C* line0, const W* __restrict__ tw, int lane)
     {
         constexpr int R = wplan_radix(N, P);
         constexpr int m = wplan_m(N, P);
         constexpr int s = N / (m * R);
         constexpr int NBF = N / R;
         constexpr int NB = (NBF + 31) / 32;
-        C v[NB][R];
+        C v[L][NB][R];
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
             const int b = lane + 32 * u;
             if (NBF % 32 == 0 || b < NBF) {
 #pragma unroll
-                for (int j = 0; j < R; ++j) v[u][j] = line[wpad<EB>(b + j * NBF)];
+                for (int i = 0; i < L; ++i)
+#pragma unroll
+                    for (int j = 0; j < R; ++j) v[i][u][j] = line0[i * LS + wpad<EB>(b + j * NBF)];
                 if (m > 1) {
                     const int k = b % m;
                     const int ks = k * s;
 #pragma unroll
-                    for (int j = 1; j < R; ++j) v[u][j] = A::mul(v[u][j], __ldg(tw + j * ks));
+                    for (int j = 1; j < R; ++j) {
+                        const W w = __ldg(tw + j * ks);
+#pragma unroll
+                        for (int i = 0; i < L; ++i) v[i][u][j] = A::mul(v[i][u][j], w);
+                    }
                 }
-                Dft<A, R>::run(v[u]);
+#pragma unroll
+                for (int i = 0; i < L; ++i) Dft<A, R>::run(v[i][u]);
             }
         }
         __syncwarp();
@@ -96,18 +107,20 @@ struct WarpLine {
                 const int t = b / m, k = b % m;
                 const int base = t * m * R + k;
 #pragma unroll
-                for (int q = 0; q < R; ++q) line[wpad<EB>(base + m * q)] = v[u][q];
+                for (int i = 0; i < L; ++i)
+#pragma unroll
+                    for (int q = 0; q < R; ++q) line0[i * LS + wpad<EB>(base + m * q)] = v[i][u][q];
             }
         }
         __syncwarp();
     }
 
-    template <int P>
-    __device__ __forceinline__ static void passes(C* line, const W* __restrict__ tw, int lane)
+    template <int P, int L = 1>
+    __device__ __forceinline__ static void passes(C* line0, const W* __restrict__ tw, int lane)
     {
         if constexpr (P < kPasses) {
-            pass<P>(line, tw, lane);
-            passes<P + 1>(line, tw, lane);
+            pass<P, L>(line0, tw, lane);
+            passes<P + 1, L>(line0, tw, lane);
         }
     }
 };
@@ -147,57 +160,67 @@ __device__ __forceinline__ void warp_fix(typename A::C* line, int lane)
     }
 }
 
-template <class A, int N, int G, bool CONTIG, bool CONJ_SCALE, bool EXT>
+template <class A, int N, int G, int L, bool CONTIG, bool CONJ_SCALE, bool EXT>
 __device__ __forceinline__ void warp_tile_store(const StageArgs& p, const TileGeom& tg,
                                                 const typename A::C* buf, int tid)
 {
     constexpr int CB = sizeof(typename A::C);
     constexpr int LS = warp_line_stride<CB>(N);
     constexpr int EB = EXT ? Io<A>::kExtBytes : Io<A>::kMidBytes;
+    constexpr int SL = 32 / L;             // threads per line of the tile
     char* first = reinterpret_cast<char*>(p.out) + tg.obase * EB;
     if constexpr (!CONTIG) {
-        // thread (g, slot): line g, frequencies slot, slot + 32, ...
+        // thread (g, slot): line g, frequencies slot, slot + SL, ...
         const int g = tid % G, slot = tid / G;
         if (g >= tg.valid) return;
         const typename A::C* line = buf + g * LS;
         char* ptr = first + (g * tg.ostride + slot * p.Sk) * EB;
-        const int64_t step = (int64_t)32 * p.Sk * EB;
+        const int64_t step = (int64_t)SL * p.Sk * EB;
 #pragma unroll 4
-        for (int k = slot; k < N; k += 32) {
+        for (int k = slot; k < N; k += SL) {
             put<A, CONJ_SCALE, EXT>(ptr, line[wpad<CB>(k)], p.scale);
             ptr += step;
         }
     } else {
-        // warp g stores its own line, which is contiguous in the output
-        const int g = tid >> 5, lane = tid & 31;
-        if (g >= tg.valid) return;
-        const typename A::C* line = buf + g * LS;
-        char* ptr = first + (int64_t)g * tg.ostride * EB;
+        // warp w stores its own lines w L + i, each contiguous in the output
+        const int lane = tid & 31;
 #pragma unroll
-        for (int u = 0; u < N / 32; ++u) {
-            const int k = lane + 32 * u;
-            put<A, CONJ_SCALE, EXT>(ptr + k * EB, line[wpad<CB>(k)], p.scale);
+        for (int i = 0; i < L; ++i) {
+            const int g = (tid >> 5) * L + i;
+            if (g >= tg.valid) return;
+            const typename A::C* line = buf + g * LS;
+            char* ptr = first + (int64_t)g * tg.ostride * EB;
+#pragma unroll
+            for (int u = 0; u < N / 32; ++u) {
+                const int k = lane + 32 * u;
+                put<A, CONJ_SCALE, EXT>(ptr + k * EB, line[wpad<CB>(k)], p.scale);
+            }
         }
     }
 }
 
-template <class A, int N, int G>
+template <class A, int N, int G, int L>
 __device__ __forceinline__ void warp_store_dispatch(const StageArgs& p, const TileGeom& tg,
                                                     const typename A::C* buf, int tid)
 {
     const bool ext = p.out_fmt != FMT_DF;
     const bool cs = p.conj_out != 0;
     if (!p.contig_store) {
-        if (cs) { if (ext) warp_tile_store<A, N, G, false, true, true>(p, tg, buf, tid); else warp_tile_store<A, N, G, false, true, false>(p, tg, buf, tid); }
-        else    { if (ext) warp_tile_store<A, N, G, false, false, true>(p, tg, buf, tid); else warp_tile_store<A, N, G, false, false, false>(p, tg, buf, tid); }
+        if (cs) { if (ext) warp_tile_store<A, N, G, L, false, true, true>(p, tg, buf, tid); else warp_tile_store<A, N, G, L, false, true, false>(p, tg, buf, tid); }
+        else    { if (ext) warp_tile_store<A, N, G, L, false, false, true>(p, tg, buf, tid); else warp_tile_store<A, N, G, L, false, false, false>(p, tg, buf, tid); }
     } else {
-        if (cs) { if (ext) warp_tile_store<A, N, G, true, true, true>(p, tg, buf, tid); else warp_tile_store<A, N, G, true, true, false>(p, tg, buf, tid); }
-        else    { if (ext) warp_tile_store<A, N, G, true, false, true>(p, tg, buf, tid); else warp_tile_store<A, N, G, true, false, false>(p, tg, buf, tid); }
+        if (cs) { if (ext) warp_tile_store<A, N, G, L, true, true, true>(p, tg, buf, tid); else warp_tile_store<A, N, G, L, true, true, false>(p, tg, buf, tid); }
+        else    { if (ext) warp_tile_store<A, N, G, L, true, false, true>(p, tg, buf, tid); else warp_tile_store<A, N, G, L, true, false, false>(p, tg, buf, tid); }
     }
 }
 
-// register budget: 128 per thread for 16-byte elements, 64-80 for 8-byte ones
-constexpr int warp_min_blocks(int T, int EB) { return EB >= 16 ? (512 / T > 0 ? 512 / T : 1) : (T >= 512 ? 2 : 3); }
+// register budget: 128 per thread for 16-byte elements and for 8-byte ones
+// in CTAs of 128 threads (two lines per warp, four CTAs per SM), 64-85 for
+// larger CTAs of 8-byte elements
+constexpr int warp_min_blocks(int T, int EB)
+{
+    return EB >= 16 ? (512 / T > 0 ? 512 / T : 1) : (T >= 512 ? 2 : (T <= 128 ? 4 : 3));
+}
 
 // Tiles are double-buffered (the next tile's copies overlap this tile's
 // passes) except for 512-point lines of 16-byte elements: there one buffer
@@ -206,35 +229,60 @@ constexpr int warp_min_blocks(int T, int EB) { return EB >= 16 ? (512 / T > 0 ? 
 template <class A, int N>
 constexpr bool warp_double_buffer() { return !(N >= 512 && sizeof(typename A::C) >= 16); }
 
+// Lines per warp: FP32 passes are short and wait on shared memory, so each
+// warp takes two lines (two independent butterflies per thread and pass, one
+// set of twiddle loads); the double-float and FP64 passes carry enough
+// arithmetic per line and need the registers.
 template <class A, int N, int G>
-__global__ void __launch_bounds__(32 * G, warp_min_blocks(32 * G, sizeof(typename A::C)))
+constexpr int warp_lines_per_warp() { return (sizeof(typename A::C) == 8 && G % 2 == 0) ? 2 : 1; }
+
+template <class A, int N, int G>
+__global__ void __launch_bounds__(32 * G / warp_lines_per_warp<A, N, G>(),
+                                  warp_min_blocks(32 * G / warp_lines_per_warp<A, N, G>(), sizeof(typename A::C)))
 fft_warp_kernel(const StageArgs p, int64_t ntiles)
 {
     using C = typename A::C;
+    constexpr int L = warp_lines_per_warp<A, N, G>();
     constexpr int LS = warp_line_stride<sizeof(C)>(N);
     constexpr bool DB = warp_double_buffer<A, N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* cur = reinterpret_cast<C*>(smem_raw);
     C* nxt = DB ? cur + G * LS : cur;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g0 = warp * L;                // this warp's first line of the tile
     const typename A::W* tw = reinterpret_cast<const typename A::W*>(p.tw);
     const bool convert = Io<A>::kConverts && p.in_fmt == FMT_C128;
 
     int64_t tile = blockIdx.x;
-    if (DB && tile < ntiles) warp_issue_load<A, N>(p, tile_geom(p, tile, G), warp, cur + warp * LS, lane);
+    if (DB && tile < ntiles) {
+        const TileGeom tg = tile_geom(p, tile, G);
+#pragma unroll
+        for (int i = 0; i < L; ++i) warp_issue_load<A, N>(p, tg, g0 + i, cur + (g0 + i) * LS, lane);
+    }
     for (; tile < ntiles; tile += gridDim.x) {
         const TileGeom tg = tile_geom(p, tile, G);
-        C* line = cur + warp * LS;
-        if (!DB) warp_issue_load<A, N>(p, tg, warp, line, lane);
+        C* line0 = cur + g0 * LS;
+        if (!DB) {
+#pragma unroll
+            for (int i = 0; i < L; ++i) warp_issue_load<A, N>(p, tg, g0 + i, line0 + i * LS, lane);
+        }
         cp_async_wait_all();
-        if (convert) { if (p.conj_in) warp_fix<A, N, true, true>(line, lane); else warp_fix<A, N, true, false>(line, lane); }
-        else if (p.conj_in) warp_fix<A, N, false, true>(line, lane);
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+            C* line = line0 + i * LS;
+            if (convert) { if (p.conj_in) warp_fix<A, N, true, true>(line, lane); else warp_fix<A, N, true, false>(line, lane); }
+            else if (p.conj_in) warp_fix<A, N, false, true>(line, lane);
+        }
         __syncwarp();
         const int64_t next = tile + gridDim.x;
-        if (DB && next < ntiles) warp_issue_load<A, N>(p, tile_geom(p, next, G), warp, nxt + warp * LS, lane);
-        WarpLine<A, N>::template passes<0>(line, tw, lane);
+        if (DB && next < ntiles) {
+            const TileGeom tn = tile_geom(p, next, G);
+#pragma unroll
+            for (int i = 0; i < L; ++i) warp_issue_load<A, N>(p, tn, g0 + i, nxt + (g0 + i) * LS, lane);
+        }
+        WarpLine<A, N>::template passes<0, L>(line0, tw, lane);
         __syncthreads();                   // every line of the tile is transformed
-        warp_store_dispatch<A, N, G>(p, tg, cur, tid);
+        warp_store_dispatch<A, N, G, L>(p, tg, cur, tid);
         __syncthreads();                   // cur becomes the next copy target
         C* t = cur; cur = nxt; nxt = t;
     }
@@ -244,7 +292,7 @@ fft_warp_kernel(const StageArgs p, int64_t ntiles)
 template <class A, int N, int G>
 cudaError_t launch_warp_n(const StageLaunch& L, cudaStream_t st)
 {
-    constexpr int T = 32 * G;
+    constexpr int T = 32 * G / warp_lines_per_warp<A, N, G>();
     const size_t smem = (warp_double_buffer<A, N>() ? 2 : 1) * (size_t)G * warp_line_stride<sizeof(typename A::C)>(N) *
                         sizeof(typename A::C);
     static int cached[kMaxDevices] = {};          // CTAs per SM on each device, 0 = not yet known
