@@ -38,6 +38,7 @@ template <class A> struct RealPair;
 
 template <> struct RealPair<ArF64> {
     using T = double;
+    static constexpr bool kDF = false;
     __device__ __forceinline__ static double2 make(double a, double b) { return make_double2(a, b); }
     __device__ __forceinline__ static double2 re_parts(double2 u, double2 v) { return make_double2(u.x, v.x); }
     __device__ __forceinline__ static double part(double2 z, int im, double s) { return (im ? z.y : z.x) * s; }
@@ -45,6 +46,7 @@ template <> struct RealPair<ArF64> {
 
 template <> struct RealPair<ArF32> {
     using T = float;
+    static constexpr bool kDF = false;
     __device__ __forceinline__ static float2 make(float a, float b) { return make_float2(a, b); }
     __device__ __forceinline__ static float2 re_parts(float2 u, float2 v) { return make_float2(u.x, v.x); }
     __device__ __forceinline__ static float part(float2 z, int im, double s) { return (im ? z.y : z.x) * (float)s; }
@@ -53,6 +55,7 @@ template <> struct RealPair<ArF32> {
 // double-float: (re.hi, im.hi, re.lo, im.lo)
 template <> struct RealPair<ArDF> {
     using T = double;
+    static constexpr bool kDF = true;
     __device__ __forceinline__ static float4 make(double a, double b) {
         const float2 ha = split_f64(a), hb = split_f64(b);
         return make_float4(ha.x, hb.x, ha.y, hb.y);
@@ -188,6 +191,34 @@ __global__ void __launch_bounds__(kStageThreads) c2r_stage_kernel(const StageArg
 
 constexpr int kRealWarpG = 8;       // complex lines (warps) per CTA
 
+// Real lines of lengths up to 256 are staged: each warp copies its two real
+// lines of the next tile into shared memory (cp.async) while the current tile
+// is transformed.  512-point lines load directly (the staging area would halve
+// the CTAs per SM).
+template <int N>
+constexpr bool r2c_staged() { return N <= 256; }
+
+// cp.async of real lines la, la + 1 (zeros beyond L) into raw[0, 2N)
+template <class T, int N>
+__device__ __forceinline__ void r2c_issue_raw(const T* __restrict__ x, int64_t L, int64_t la, T* raw, int lane)
+{
+    constexpr int PER = 16 / (int)sizeof(T);     // reals per 16-byte copy
+    constexpr int CH = N / PER;                  // copies per line
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        T* dst = raw + h * N;
+        if (la + h < L) {
+            const T* src = x + (la + h) * N;
+#pragma unroll
+            for (int c = lane; c < CH; c += 32) cp_async<16>(dst + c * PER, src + c * PER);
+        } else {
+#pragma unroll
+            for (int pos = lane; pos < N; pos += 32) dst[pos] = T(0);
+        }
+    }
+    cp_async_commit();
+}
+
 // Forward real stage, power-of-two N: warp w of tile t takes real lines
 // l0 + 2w and l0 + 2w + 1 (l0 = 2 G t); the CTA then separates the spectra of
 // its 2G lines and stores frequency k of all of them (2G consecutive
@@ -202,6 +233,7 @@ r2c_warp_kernel(const StageArgs p, int64_t ntiles)
     constexpr int EB = sizeof(C);
     constexpr int LS = warp_line_stride<EB>(N);
     constexpr int TWO = 2 * G, SLOTS = 32 * G / TWO;
+    constexpr bool STAGED = r2c_staged<N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tile = reinterpret_cast<C*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -209,19 +241,35 @@ r2c_warp_kernel(const StageArgs p, int64_t ntiles)
     const T* x = reinterpret_cast<const T*>(p.in);
     const int64_t L = p.M1;
     C* line = tile + warp * LS;
+    T* raw = reinterpret_cast<T*>(tile + G * LS) + warp * 2 * N;     // this warp's staged real lines
     const int o = tid % TWO, slot = tid / TWO;          // store phase: line o of the tile
     const C* oline = tile + (o >> 1) * LS;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int64_t t = blockIdx.x;
+    if (STAGED && t < ntiles) r2c_issue_raw<T, N>(x, L, t * TWO + 2 * warp, raw, lane);
+    for (; t < ntiles; t += gridDim.x) {
         const int64_t l0 = t * TWO;
         const int64_t la = l0 + 2 * warp, lb = la + 1;
+        if constexpr (STAGED) {
+            cp_async_wait_all();
+            __syncwarp();
 #pragma unroll
-        for (int u = 0; u < N / 32; ++u) {
-            const int pos = lane + 32 * u;
-            const T a = la < L ? x[la * N + pos] : T(0);
-            const T b = lb < L ? x[lb * N + pos] : T(0);
-            line[wpad<EB>(pos)] = RP::make(a, b);
+            for (int u = 0; u < N / 32; ++u) {
+                const int pos = lane + 32 * u;
+                line[wpad<EB>(pos)] = RP::make(raw[pos], raw[N + pos]);
+            }
+            __syncwarp();                                // raw is consumed: refill it with the next tile
+            const int64_t tn = t + gridDim.x;
+            if (tn < ntiles) r2c_issue_raw<T, N>(x, L, tn * TWO + 2 * warp, raw, lane);
+        } else {
+#pragma unroll
+            for (int u = 0; u < N / 32; ++u) {
+                const int pos = lane + 32 * u;
+                const T a = la < L ? x[la * N + pos] : T(0);
+                const T b = lb < L ? x[lb * N + pos] : T(0);
+                line[wpad<EB>(pos)] = RP::make(a, b);
+            }
+            __syncwarp();
         }
-        __syncwarp();
         WarpLine<A, N>::template passes<0>(line, tw, lane);
         __syncthreads();                                 // every line of the tile is transformed
         const int64_t l = l0 + o;
@@ -235,10 +283,38 @@ r2c_warp_kernel(const StageArgs p, int64_t ntiles)
         }
         __syncthreads();                                 // the tile buffer is free again
     }
+    cp_async_wait_all();
+}
+
+// Format of the inverse real stage's input that the staged copy keeps as it is
+// (the arithmetic's own element): double-float pairs, complex64, complex128.
+template <class A>
+constexpr int c2r_raw_fmt() { return sizeof(typename A::C) == 8 ? FMT_C64 : (RealPair<A>::kDF ? FMT_DF : FMT_C128); }
+
+// cp.async of half lines la, la + 1 (NH elements each; zeros beyond L) into raw[0, 2 NH)
+template <class A, int NH>
+__device__ __forceinline__ void c2r_issue_raw(const typename A::C* __restrict__ in, int64_t L, int64_t la,
+                                              typename A::C* raw, int lane)
+{
+    constexpr int EB = sizeof(typename A::C);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        typename A::C* dst = raw + h * NH;
+        if (la + h < L) {
+            const typename A::C* src = in + (la + h) * NH;
+            for (int k = lane; k < NH; k += 32) cp_async<EB>(dst + k, src + k);
+        } else {
+            for (int k = lane; k < NH; k += 32) dst[k] = A::zero();
+        }
+    }
+    cp_async_commit();
 }
 
 // Inverse real stage, power-of-two N: warp w of tile t extends half lines
-// l0 + 2w and l0 + 2w + 1, transforms, and writes the two real lines.
+// l0 + 2w and l0 + 2w + 1, transforms, and writes the two real lines.  For
+// N <= 256 with input in the arithmetic's own format, each warp copies its
+// two half lines of the next tile into shared memory (cp.async) while the
+// current tile is transformed.
 template <class A, int N, int G>
 __global__ void __launch_bounds__(32 * G, warp_min_blocks(32 * G, sizeof(typename A::C)))
 c2r_warp_kernel(const StageArgs p, int64_t ntiles)
@@ -256,11 +332,26 @@ c2r_warp_kernel(const StageArgs p, int64_t ntiles)
     T* y = reinterpret_cast<T*>(p.out);
     const int64_t L = p.M1;
     C* line = tile + warp * LS;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    C* raw = tile + G * LS + warp * 2 * NH;              // this warp's staged half lines
+    const bool staged = r2c_staged<N>() && p.in_fmt == c2r_raw_fmt<A>();
+    const C* in = reinterpret_cast<const C*>(p.in);
+    int64_t t = blockIdx.x;
+    if (staged && t < ntiles) c2r_issue_raw<A, NH>(in, L, t * 2 * G + 2 * warp, raw, lane);
+    for (; t < ntiles; t += gridDim.x) {
         const int64_t la = t * 2 * G + 2 * warp, lb = la + 1;
+        if (staged) {
+            cp_async_wait_all();
+            __syncwarp();
+        }
         for (int k = lane; k < NH; k += 32) {
-            const C v1 = la < L ? Io<A>::load(p.in, p.in_fmt, la * NH + k) : A::zero();
-            const C v2 = lb < L ? Io<A>::load(p.in, p.in_fmt, lb * NH + k) : A::zero();
+            C v1, v2;
+            if (staged) {
+                v1 = raw[k];
+                v2 = raw[NH + k];
+            } else {
+                v1 = la < L ? Io<A>::load(p.in, p.in_fmt, la * NH + k) : A::zero();
+                v2 = lb < L ? Io<A>::load(p.in, p.in_fmt, lb * NH + k) : A::zero();
+            }
             if (k == 0 || 2 * k == N) {
                 line[wpad<EB>(k)] = RP::re_parts(v1, v2);
             } else {
@@ -269,6 +360,10 @@ c2r_warp_kernel(const StageArgs p, int64_t ntiles)
             }
         }
         __syncwarp();
+        if (staged) {                                    // raw is consumed: refill it with the next tile
+            const int64_t tn = t + gridDim.x;
+            if (tn < ntiles) c2r_issue_raw<A, NH>(in, L, tn * 2 * G + 2 * warp, raw, lane);
+        }
         WarpLine<A, N>::template passes<0>(line, tw, lane);
 #pragma unroll
         for (int u = 0; u < N / 32; ++u) {
@@ -279,15 +374,20 @@ c2r_warp_kernel(const StageArgs p, int64_t ntiles)
         }
         __syncwarp();                                    // the line is free again
     }
+    cp_async_wait_all();
 }
 
 template <class A, int N>
 cudaError_t launch_real_warp(const StageLaunch& L, cudaStream_t st)
 {
     constexpr int G = kRealWarpG;
-    const size_t smem = (size_t)G * warp_line_stride<sizeof(typename A::C)>(N) * sizeof(typename A::C);
-    static int cached_r2c[kMaxDevices] = {}, cached_c2r[kMaxDevices] = {};   // CTAs per SM, 0 = unknown
     const bool fwd = L.family == KERNEL_R2C;
+    // tile of G complex lines, and for the staged forward kernel the 2G real lines of the next tile
+    const size_t smem = (size_t)G * warp_line_stride<sizeof(typename A::C)>(N) * sizeof(typename A::C) +
+                        (!r2c_staged<N>() ? 0
+                         : fwd ? (size_t)G * 2 * N * sizeof(typename RealPair<A>::T)
+                               : (size_t)G * 2 * (N / 2 + 1) * sizeof(typename A::C));
+    static int cached_r2c[kMaxDevices] = {}, cached_c2r[kMaxDevices] = {};   // CTAs per SM, 0 = unknown
     int* slot = device_slot(fwd ? cached_r2c : cached_c2r);
     int per_sm = slot ? *slot : 0;
     if (per_sm == 0) {
