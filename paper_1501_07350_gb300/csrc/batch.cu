@@ -93,7 +93,7 @@ __device__ __forceinline__ bool tile_ok(const StageArgs& p)
 // Shared-memory layout of the batched kernel: [tile buffer | queue prefix
 // item_base (3 count + 1 int64) | tile counts need (3 count uint32)].
 template <class A, int G>
-__global__ void __launch_bounds__(kBatchThreads, 2)
+__global__ void __launch_bounds__(kBatchThreads, sizeof(typename A::C) == 8 ? 3 : 2)
 batch_kernel(const BatchDev d, size_t buf_bytes)
 {
     using C = typename A::C;
