@@ -36,33 +36,50 @@ namespace {
 // Two real values <-> one complex element, per arithmetic.
 template <class A> struct RealPair;
 
+// Scale is the output factor in the form `part` applies it (prepared once per
+// thread by scale_of).
 template <> struct RealPair<ArF64> {
     using T = double;
+    using Scale = double;
     static constexpr bool kDF = false;
     __device__ __forceinline__ static double2 make(double a, double b) { return make_double2(a, b); }
     __device__ __forceinline__ static double2 re_parts(double2 u, double2 v) { return make_double2(u.x, v.x); }
-    __device__ __forceinline__ static double part(double2 z, int im, double s) { return (im ? z.y : z.x) * s; }
+    __device__ __forceinline__ static Scale scale_of(double s) { return s; }
+    __device__ __forceinline__ static double part(double2 z, int im, Scale s) { return (im ? z.y : z.x) * s; }
 };
 
 template <> struct RealPair<ArF32> {
     using T = float;
+    using Scale = float;
     static constexpr bool kDF = false;
     __device__ __forceinline__ static float2 make(float a, float b) { return make_float2(a, b); }
     __device__ __forceinline__ static float2 re_parts(float2 u, float2 v) { return make_float2(u.x, v.x); }
-    __device__ __forceinline__ static float part(float2 z, int im, double s) { return (im ? z.y : z.x) * (float)s; }
+    __device__ __forceinline__ static Scale scale_of(double s) { return (float)s; }
+    __device__ __forceinline__ static float part(float2 z, int im, Scale s) { return (im ? z.y : z.x) * s; }
 };
 
-// double-float: (re.hi, im.hi, re.lo, im.lo)
+// double-float: (re.hi, im.hi, re.lo, im.lo).  The output factor is split
+// into floats (kh + kl) once, and the product is formed in double-float on
+// the FP32 units (exact kh * hi plus first-order terms) before the single
+// FP64 addition of the join.
 template <> struct RealPair<ArDF> {
     using T = double;
+    using Scale = float2;
     static constexpr bool kDF = true;
     __device__ __forceinline__ static float4 make(double a, double b) {
         const float2 ha = split_f64(a), hb = split_f64(b);
         return make_float4(ha.x, hb.x, ha.y, hb.y);
     }
     __device__ __forceinline__ static float4 re_parts(float4 u, float4 v) { return make_float4(u.x, v.x, u.z, v.z); }
-    __device__ __forceinline__ static double part(float4 z, int im, double s) {
-        return (im ? join_f64(z.y, z.w) : join_f64(z.x, z.z)) * s;
+    __device__ __forceinline__ static Scale scale_of(double s) {
+        const float kh = (float)s;
+        return make_float2(kh, (float)(s - (double)kh));
+    }
+    __device__ __forceinline__ static double part(float4 z, int im, Scale k) {
+        const float h = im ? z.y : z.x, l = im ? z.w : z.z;
+        const float ph = __fmul_rn(h, k.x);
+        const float pl = __fmaf_rn(l, k.x, __fmaf_rn(h, k.y, __fmaf_rn(h, k.x, -ph)));
+        return join_f64(ph, pl);
     }
 };
 
@@ -155,6 +172,7 @@ __global__ void __launch_bounds__(kStageThreads) c2r_stage_kernel(const StageArg
     C* buf0 = reinterpret_cast<C*>(smem_raw);
     C* buf1 = buf0 + (size_t)n * ld;
     const int64_t L = p.M1, l0 = (int64_t)blockIdx.x * 2 * G;
+    const typename RP::Scale ks = RP::scale_of(p.scale);
     {   // half lines l0 + 2j, l0 + 2j + 1 -> Hermitian-extended complex line j
         const int dj = kStageThreads / nh, dk = kStageThreads - dj * nh;
         int j = tid / nh, k = tid - j * nh;
@@ -180,7 +198,7 @@ __global__ void __launch_bounds__(kStageThreads) c2r_stage_kernel(const StageArg
         int o = tid / n, i = tid - o * n;
         for (int e = tid; e < 2 * G * n; e += kStageThreads) {
             const int64_t l = l0 + o;
-            if (l < L) y[l * n + i] = (T)RP::part(cur[i * ld + (o >> 1)], o & 1, p.scale);
+            if (l < L) y[l * n + i] = (T)RP::part(cur[i * ld + (o >> 1)], o & 1, ks);
             i += di; o += dout;
             if (i >= n) { i -= n; ++o; }
         }
@@ -335,6 +353,7 @@ c2r_warp_kernel(const StageArgs p, int64_t ntiles)
     C* raw = tile + G * LS + warp * 2 * NH;              // this warp's staged half lines
     const bool staged = r2c_staged<N>() && p.in_fmt == c2r_raw_fmt<A>();
     const C* in = reinterpret_cast<const C*>(p.in);
+    const typename RP::Scale ks = RP::scale_of(p.scale);
     int64_t t = blockIdx.x;
     if (staged && t < ntiles) c2r_issue_raw<A, NH>(in, L, t * 2 * G + 2 * warp, raw, lane);
     for (; t < ntiles; t += gridDim.x) {
@@ -369,8 +388,8 @@ c2r_warp_kernel(const StageArgs p, int64_t ntiles)
         for (int u = 0; u < N / 32; ++u) {
             const int pos = lane + 32 * u;
             const C z = line[wpad<EB>(pos)];
-            if (la < L) y[la * N + pos] = (T)RP::part(z, 0, p.scale);
-            if (lb < L) y[lb * N + pos] = (T)RP::part(z, 1, p.scale);
+            if (la < L) y[la * N + pos] = (T)RP::part(z, 0, ks);
+            if (lb < L) y[lb * N + pos] = (T)RP::part(z, 1, ks);
         }
         __syncwarp();                                    // the line is free again
     }
