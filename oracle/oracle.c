@@ -18,7 +18,7 @@
  *                 pack a send buffer per destination, communicate, unpack
  *                 and merge into the next decomposition.
  *
- * Readings where the paper is silent (each is listed in the design doc):
+ * Readings where the paper is silent:
  *   - stage s transforms the fastest axis of its ordering: c in abc, b in
  *     cab, a in cba (each rank owns complete lines of that axis);
  *   - the degree (1-D or 2-D) is chosen per ordering from its own leading
