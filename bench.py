@@ -93,6 +93,27 @@ def profiled_traffic(kernel_hash: str, family: str, G: int):
     return None
 
 
+def df_ops_per_point(n: int) -> float:
+    """FP32 operations per point of one double-float stage over lines of n =
+    2^k points, as the warp kernel's radix plan runs them: the remainder radix
+    (2 or 4) first, then radix 8.  A double-float complex addition costs 16
+    operations (TwoSum plus the lo sum, per real part), a twiddle product 32.
+    Per point: radix 2 = 16, radix 4 = 32, radix 8 = 54 (24 additions and two
+    multiplications by (1 - i)/sqrt 2 per 8 points), plus (R - 1)/R x 32 for
+    the twiddles of every pass after the first."""
+    per = {2: 16.0, 4: 32.0, 8: 54.0}
+    radices, m = [], n
+    while m % 8 == 0:
+        m //= 8
+        radices.append(8)
+    if m > 1:
+        radices.insert(0, m)
+    ops = 0.0
+    for i, r in enumerate(radices):
+        ops += per[r] + (32.0 * (r - 1) / r if i > 0 else 0.0)
+    return ops
+
+
 def dominant_kernel(chosen: dict):
     """(family, G) that most of the timed plans use (ties: the first P)."""
     fam = {0: "warp", 1: "warp", 2: "tile", 3: "generic"}
@@ -274,6 +295,19 @@ def run_ours(args, rank, world, local_rank):
                 "peak_kind": peak_kind,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_us": round(avg_s * 1e6, 2),
                 "share_of_step": round(fft_ms / max(1e-9, phases["exec"]["ms"]), 4)}
+    if arith_name == "ArDF":
+        # the binding resource of the double-float kernel: FP32-pipe issue
+        ops = df_ops_per_point(n)
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = clocks.get("sm_max_mhz") or 2070.0
+        alu_peak = sms * 128 * mhz * 1e6 / 1e9
+        alu_ach = ops * N / avg_s / 1e9
+        roofline["alu"] = {"bound": "alu", "unit": "G FP32 ops/s", "ops_per_point": ops,
+                           "achieved": round(alu_ach, 1), "peak": round(alu_peak, 1),
+                           "frac": round(alu_ach / alu_peak, 4),
+                           "peak_kind": "SMs x 128 FP32 lanes x max SM clock (%d MHz)" % mhz,
+                           "ops": "double-float arithmetic of the radix passes only (no conversions, "
+                                  "loads or index math)"}
 
     # end to end through the host-buffer C ABI call (copies inside the timed region)
     y_host = torch.empty_like(x_host).pin_memory()
