@@ -174,6 +174,15 @@ int openfft_exec_c2r(openfft_plan_t plan, const void* in, void* out);
  * whole transform instead. */
 int openfft_exec_c2c_host(openfft_plan_t plan, const void* host_in, void* host_out, int dir);
 
+/* openfft_exec_c2c_host without the final wait: returns once the copies and
+ * launches are enqueued.  `host_in` must stay unchanged and `host_out`
+ * unread until openfft_sync(plan) returns (it waits for the plan's copy
+ * stream and its stream).  Successive calls on one plan run in order.  Calls
+ * on different plans may overlap their copies: the host-to-device copy of one
+ * plan can run beside the device-to-host copy of another.  Same results, bit
+ * for bit, as the synchronous call. */
+int openfft_exec_c2c_host_async(openfft_plan_t plan, const void* host_in, void* host_out, int dir);
+
 /* Number of line ranges of openfft_exec_c2c_host: 1 (no overlap) to 32;
  * 0 (the default) takes one per 8 MiB of the array, 1 to 16.  INVALID_ARG
  * outside 0..32. */

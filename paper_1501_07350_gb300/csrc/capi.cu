@@ -903,7 +903,25 @@ int openfft_set_host_chunks(openfft_plan_t plan, int chunks)
     return OPENFFT_OK;
 }
 
+namespace {
+int exec_host(openfft_plan_t plan, const void* host_in, void* host_out, int dir, bool wait);
+}
+
 int openfft_exec_c2c_host(openfft_plan_t plan, const void* host_in, void* host_out, int dir)
+{
+    return exec_host(plan, host_in, host_out, dir, true);
+}
+
+int openfft_exec_c2c_host_async(openfft_plan_t plan, const void* host_in, void* host_out, int dir)
+{
+    return exec_host(plan, host_in, host_out, dir, false);
+}
+
+namespace {
+
+// Host-buffer execution; with `wait` false it returns once everything is
+// enqueued (openfft_sync waits for the copies as well).
+int exec_host(openfft_plan_t plan, const void* host_in, void* host_out, int dir, bool wait)
 {
     if (!plan || !host_in || !host_out) return fail(OPENFFT_ERR_INVALID_ARG, "null plan or buffer");
     if (plan->batch) return fail(OPENFFT_ERR_INVALID_ARG, "batched plan: use openfft_exec_many");
@@ -927,7 +945,7 @@ int openfft_exec_c2c_host(openfft_plan_t plan, const void* host_in, void* host_o
         int st = run_ops(plan, ops, plan->stage_in, plan->stage_out, arith);
         if (st) return st;
         if ((e = cudaMemcpyAsync(host_out, plan->stage_out, bytes, cudaMemcpyDeviceToHost, plan->stream))) return cuda_fail(e, "D2H");
-        if ((e = cudaStreamSynchronize(plan->stream))) return cuda_fail(e, "sync");
+        if (wait && (e = cudaStreamSynchronize(plan->stream))) return cuda_fail(e, "sync");
         return OPENFFT_OK;
     }
     // Copies run on a second stream, range by range: the first stage starts
@@ -999,10 +1017,13 @@ int openfft_exec_c2c_host(openfft_plan_t plan, const void* host_in, void* host_o
             (e = cudaMemcpyAsync(hout, dout, bytes, cudaMemcpyDeviceToHost, cs)))
             return cuda_fail(e, "D2H");
     }
+    if (!wait) return OPENFFT_OK;
     if ((e = cudaStreamSynchronize(cs))) return cuda_fail(e, "sync");
     if ((e = cudaStreamSynchronize(st))) return cuda_fail(e, "sync");
     return OPENFFT_OK;
 }
+
+}  // namespace
 
 int openfft_sync(openfft_plan_t plan)
 {
@@ -1012,8 +1033,9 @@ int openfft_sync(openfft_plan_t plan)
         if (e) return cuda_fail(e, "stream synchronize");
         return batch_status(plan->batch, &fail_cstr);
     }
-    cudaError_t e = cudaStreamSynchronize(plan->stream);
-    if (e) return cuda_fail(e, "stream synchronize");
+    cudaError_t e;
+    if (plan->copy_stream && (e = cudaStreamSynchronize(plan->copy_stream))) return cuda_fail(e, "copy stream synchronize");
+    if ((e = cudaStreamSynchronize(plan->stream))) return cuda_fail(e, "stream synchronize");
     int st = 0;
     if (plan->d_status) {
         if ((e = cudaMemcpy(&st, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost))) return cuda_fail(e, "status word");
