@@ -183,6 +183,16 @@ int openfft_exec_c2c_host(openfft_plan_t plan, const void* host_in, void* host_o
  * for bit, as the synchronous call. */
 int openfft_exec_c2c_host_async(openfft_plan_t plan, const void* host_in, void* host_out, int dir);
 
+/* Streams of the host-buffer calls' copies: uploads on `h2d`, downloads on
+ * `d2h` (each a cudaStream_t).  Both NULL (the default) = two streams the
+ * plan creates and owns.  Plans given the same two streams queue their
+ * transfers in call order across plans, so one plan's upload runs beside
+ * another's download instead of sharing the link with the other uploads.
+ * The caller keeps the streams alive while the plan may use them; copies
+ * already queued on the previous streams are waited for first.  INVALID_ARG
+ * if exactly one of the two is NULL. */
+int openfft_set_copy_streams(openfft_plan_t plan, void* h2d, void* d2h);
+
 /* Number of line ranges of openfft_exec_c2c_host: 1 (no overlap) to 32;
  * 0 (the default) takes one per 8 MiB of the array, 1 to 16.  INVALID_ARG
  * outside 0..32. */

@@ -116,8 +116,12 @@ struct openfft_plan_s {
     std::vector<Op> ops_fwd, ops_bwd;
     void* stage_in = nullptr;     // host-exec staging (lazy)
     void* stage_out = nullptr;
-    cudaStream_t copy_stream = nullptr;            // host-exec copies (lazy)
-    cudaEvent_t host_ev[2 * kMaxHostChunks + 1] = {};
+    // host-exec copies: plan-owned upload / download streams (lazy), or the
+    // caller's (openfft_set_copy_streams)
+    cudaStream_t own_h2d = nullptr, own_d2h = nullptr;
+    cudaStream_t user_h2d = nullptr, user_d2h = nullptr;
+    bool user_copy_streams = false;
+    cudaEvent_t host_ev[2 * kMaxHostChunks + 2] = {};   // ranges in, ranges out, stage 1 read, download done
     int host_chunks = 0;                           // 0 = chosen by size
     // execution-time breakdown
     bool timing = false;
@@ -497,7 +501,9 @@ void free_plan(openfft_plan_s* p)
         cudaFree(T.d_C); cudaFree(T.d_sdispl); cudaFree(T.d_rdispl);
     }
     cudaFree(p->stage_in); cudaFree(p->stage_out);
-    if (p->copy_stream) { cudaStreamSynchronize(p->copy_stream); cudaStreamDestroy(p->copy_stream); }
+    if (p->user_copy_streams) { cudaStreamSynchronize(p->user_h2d); cudaStreamSynchronize(p->user_d2h); }
+    if (p->own_h2d) { cudaStreamSynchronize(p->own_h2d); cudaStreamDestroy(p->own_h2d); }
+    if (p->own_d2h) { cudaStreamSynchronize(p->own_d2h); cudaStreamDestroy(p->own_d2h); }
     for (cudaEvent_t e : p->host_ev) if (e) cudaEventDestroy(e);
     cudaFree(p->d_status);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
@@ -826,6 +832,23 @@ int openfft_exec_c2r(openfft_plan_t plan, const void* in, void* out)
 
 namespace {
 
+// The streams of host-exec copies: the caller's, or plan-owned ones created
+// on first use (with the plan's copy events).
+cudaStream_t h2d_stream(const openfft_plan_s* p) { return p->user_copy_streams ? p->user_h2d : p->own_h2d; }
+cudaStream_t d2h_stream(const openfft_plan_s* p) { return p->user_copy_streams ? p->user_d2h : p->own_d2h; }
+
+cudaError_t ensure_copy_streams(openfft_plan_s* p)
+{
+    cudaError_t e;
+    if (!p->host_ev[0])
+        for (cudaEvent_t& ev : p->host_ev)
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming))) return e;
+    if (p->user_copy_streams) return cudaSuccess;
+    if (!p->own_h2d && (e = cudaStreamCreateWithFlags(&p->own_h2d, cudaStreamNonBlocking))) return e;
+    if (!p->own_d2h && (e = cudaStreamCreateWithFlags(&p->own_d2h, cudaStreamNonBlocking))) return e;
+    return cudaSuccess;
+}
+
 int fmt_bytes(int fmt)
 {
     return fmt == FMT_C64 || fmt == FMT_R64 ? 8 : (fmt == FMT_R32 ? 4 : 16);
@@ -907,6 +930,25 @@ namespace {
 int exec_host(openfft_plan_t plan, const void* host_in, void* host_out, int dir, bool wait);
 }
 
+int openfft_set_copy_streams(openfft_plan_t plan, void* h2d, void* d2h)
+{
+    if (!plan) return fail(OPENFFT_ERR_INVALID_ARG, "null plan");
+    if ((h2d == nullptr) != (d2h == nullptr))
+        return fail(OPENFFT_ERR_INVALID_ARG, "give both copy streams, or neither for the plan's own");
+    // copies already queued on the streams being replaced finish first
+    cudaError_t e;
+    if (plan->user_copy_streams &&
+        ((e = cudaStreamSynchronize(plan->user_h2d)) || (e = cudaStreamSynchronize(plan->user_d2h))))
+        return cuda_fail(e, "copy stream synchronize");
+    if ((plan->own_h2d && (e = cudaStreamSynchronize(plan->own_h2d))) ||
+        (plan->own_d2h && (e = cudaStreamSynchronize(plan->own_d2h))))
+        return cuda_fail(e, "copy stream synchronize");
+    plan->user_copy_streams = h2d != nullptr;
+    plan->user_h2d = (cudaStream_t)h2d;
+    plan->user_d2h = (cudaStream_t)d2h;
+    return OPENFFT_OK;
+}
+
 int openfft_exec_c2c_host(openfft_plan_t plan, const void* host_in, void* host_out, int dir)
 {
     return exec_host(plan, host_in, host_out, dir, true);
@@ -938,34 +980,45 @@ int exec_host(openfft_plan_t plan, const void* host_in, void* host_out, int dir,
     const std::vector<Op>& ops = dir == OPENFFT_FORWARD ? plan->ops_fwd : plan->ops_bwd;
     const int arith = plan->cands[(size_t)plan->current].arith;
     cudaError_t e;
+    if ((e = ensure_copy_streams(plan))) return cuda_fail(e, "copy streams");
+    cudaEvent_t ev_read = plan->host_ev[2 * kMaxHostChunks];          // stage 1 has read the staging input
+    cudaEvent_t ev_sent = plan->host_ev[2 * kMaxHostChunks + 1];      // the download of the staging output is done
     if (plan->timing || ops.size() < 3) {
-        // one copy each way around the whole transform (the phase timer
-        // brackets whole ops)
-        if ((e = cudaMemcpyAsync(plan->stage_in, host_in, bytes, cudaMemcpyHostToDevice, plan->stream))) return cuda_fail(e, "H2D");
-        int st = run_ops(plan, ops, plan->stage_in, plan->stage_out, arith);
-        if (st) return st;
-        if ((e = cudaMemcpyAsync(host_out, plan->stage_out, bytes, cudaMemcpyDeviceToHost, plan->stream))) return cuda_fail(e, "D2H");
-        if (wait && (e = cudaStreamSynchronize(plan->stream))) return cuda_fail(e, "sync");
+        // one copy each way around the whole transform, on the plan's stream
+        // (the phase timer brackets whole ops)
+        cudaStream_t st = plan->stream;
+        if ((e = cudaStreamWaitEvent(st, ev_sent, 0)) ||
+            (e = cudaMemcpyAsync(plan->stage_in, host_in, bytes, cudaMemcpyHostToDevice, st))) return cuda_fail(e, "H2D");
+        int status = run_ops(plan, ops, plan->stage_in, plan->stage_out, arith);
+        if (status) return status;
+        if ((e = cudaMemcpyAsync(host_out, plan->stage_out, bytes, cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaEventRecord(ev_read, st)) || (e = cudaEventRecord(ev_sent, st)))
+            return cuda_fail(e, "D2H");
+        if (wait && (e = cudaStreamSynchronize(st))) return cuda_fail(e, "sync");
         return OPENFFT_OK;
     }
-    // Copies run on a second stream, range by range: the first stage starts
-    // on each range of lines as soon as it has arrived, and each range of the
-    // last stage's output leaves as soon as it is written.
-    if (!plan->copy_stream) {
-        if ((e = cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking))) return cuda_fail(e, "copy stream");
-        for (cudaEvent_t& ev : plan->host_ev)
-            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming))) return cuda_fail(e, "copy events");
-    }
-    cudaStream_t st = plan->stream, cs = plan->copy_stream;
-    cudaEvent_t* ev_in = plan->host_ev + 1;
-    cudaEvent_t* ev_out = plan->host_ev + 1 + kMaxHostChunks;
+    // Uploads and downloads run on their own streams, range by range: the
+    // first stage starts on each range of lines as soon as it has arrived, and
+    // each range of the last stage's output leaves as soon as it is written.
+    cudaStream_t st = plan->stream, hs = h2d_stream(plan), ds = d2h_stream(plan);
+    cudaEvent_t* ev_in = plan->host_ev;
+    cudaEvent_t* ev_out = plan->host_ev + kMaxHostChunks;
     const int k = host_ranges(plan, bytes);
     const char* hin = static_cast<const char*>(host_in);
     char* hout = static_cast<char*>(host_out);
     char* din = static_cast<char*>(plan->stage_in);
     char* dout = static_cast<char*>(plan->stage_out);
-    // the copies into the staging array wait for work already queued on the plan's stream
-    if ((e = cudaEventRecord(plan->host_ev[0], st)) || (e = cudaStreamWaitEvent(cs, plan->host_ev[0], 0))) return cuda_fail(e, "copy order");
+    // Across calls on this plan, which run in order: the upload waits until
+    // the previous call's download is done (that also covers its first stage
+    // reading the staging input, and a host buffer this call reads that the
+    // previous call writes).  This call's work on the plan's stream, which
+    // writes the staging output, waits for that download as well.  Events
+    // never recorded make these waits no-ops.  Calls on other plans are not
+    // ordered against this one: with shared copy streams, one plan's upload
+    // can run beside another's download.
+    if ((e = cudaStreamWaitEvent(hs, ev_read, 0)) || (e = cudaStreamWaitEvent(hs, ev_sent, 0)) ||
+        (e = cudaStreamWaitEvent(st, ev_sent, 0)))
+        return cuda_fail(e, "copy order");
     const Op& first = ops.front();
     const Op& last = ops.back();
     size_t i0 = 0, i1 = ops.size();
@@ -976,8 +1029,8 @@ int exec_host(openfft_plan_t plan, const void* host_in, void* host_out, int dir,
         for (size_t j = 0; j + 1 < b.size(); ++j) {
             int64_t io, oo, lines;
             stage_lines(first.stage, b[j], b[j + 1], &io, &oo, &lines);
-            if ((e = cudaMemcpyAsync(din + io * Ein, hin + io * Ein, (size_t)(lines * a.n * Ein), cudaMemcpyHostToDevice, cs)) ||
-                (e = cudaEventRecord(ev_in[j], cs)))
+            if ((e = cudaMemcpyAsync(din + io * Ein, hin + io * Ein, (size_t)(lines * a.n * Ein), cudaMemcpyHostToDevice, hs)) ||
+                (e = cudaEventRecord(ev_in[j], hs)))
                 return cuda_fail(e, "H2D");
         }
         char* d = static_cast<char*>(resolve(plan, first.dst, din, dout));
@@ -988,9 +1041,10 @@ int exec_host(openfft_plan_t plan, const void* host_in, void* host_out, int dir,
             L.args.out = d + oo * Eout;
             if ((e = cudaStreamWaitEvent(st, ev_in[j], 0)) || (e = launch_stage(L, st))) return cuda_fail(e, "first stage");
         }
+        if ((e = cudaEventRecord(ev_read, st))) return cuda_fail(e, "copy order");
         i0 = 1;
     } else {
-        if ((e = cudaMemcpyAsync(din, hin, bytes, cudaMemcpyHostToDevice, cs)) || (e = cudaEventRecord(ev_in[0], cs)) ||
+        if ((e = cudaMemcpyAsync(din, hin, bytes, cudaMemcpyHostToDevice, hs)) || (e = cudaEventRecord(ev_in[0], hs)) ||
             (e = cudaStreamWaitEvent(st, ev_in[0], 0)))
             return cuda_fail(e, "H2D");
     }
@@ -998,6 +1052,7 @@ int exec_host(openfft_plan_t plan, const void* host_in, void* host_out, int dir,
     if (split_out) i1 = ops.size() - 1;
     int status = run_ops(plan, ops, din, dout, arith, i0, i1);
     if (status) return status;
+    if (i0 == 0 && (e = cudaEventRecord(ev_read, st))) return cuda_fail(e, "copy order");
     if (split_out) {
         const StageArgs& a = last.stage.args;
         const std::vector<int64_t> b = line_ranges(a, k);
@@ -1008,17 +1063,18 @@ int exec_host(openfft_plan_t plan, const void* host_in, void* host_out, int dir,
             StageLaunch L = stage_lines(last.stage, b[j], b[j + 1], &io, &oo, &lines);
             L.args.in = s + io * Ein;
             L.args.out = dout + oo * Eout;
-            if ((e = launch_stage(L, st)) || (e = cudaEventRecord(ev_out[j], st)) || (e = cudaStreamWaitEvent(cs, ev_out[j], 0)) ||
-                (e = cudaMemcpyAsync(hout + oo * Eout, dout + oo * Eout, (size_t)(lines * a.n * Eout), cudaMemcpyDeviceToHost, cs)))
+            if ((e = launch_stage(L, st)) || (e = cudaEventRecord(ev_out[j], st)) || (e = cudaStreamWaitEvent(ds, ev_out[j], 0)) ||
+                (e = cudaMemcpyAsync(hout + oo * Eout, dout + oo * Eout, (size_t)(lines * a.n * Eout), cudaMemcpyDeviceToHost, ds)))
                 return cuda_fail(e, "last stage");
         }
     } else {
-        if ((e = cudaEventRecord(ev_out[0], st)) || (e = cudaStreamWaitEvent(cs, ev_out[0], 0)) ||
-            (e = cudaMemcpyAsync(hout, dout, bytes, cudaMemcpyDeviceToHost, cs)))
+        if ((e = cudaEventRecord(ev_out[0], st)) || (e = cudaStreamWaitEvent(ds, ev_out[0], 0)) ||
+            (e = cudaMemcpyAsync(hout, dout, bytes, cudaMemcpyDeviceToHost, ds)))
             return cuda_fail(e, "D2H");
     }
+    if ((e = cudaEventRecord(ev_sent, ds))) return cuda_fail(e, "copy order");
     if (!wait) return OPENFFT_OK;
-    if ((e = cudaStreamSynchronize(cs))) return cuda_fail(e, "sync");
+    if ((e = cudaStreamSynchronize(ds))) return cuda_fail(e, "sync");
     if ((e = cudaStreamSynchronize(st))) return cuda_fail(e, "sync");
     return OPENFFT_OK;
 }
@@ -1034,7 +1090,9 @@ int openfft_sync(openfft_plan_t plan)
         return batch_status(plan->batch, &fail_cstr);
     }
     cudaError_t e;
-    if (plan->copy_stream && (e = cudaStreamSynchronize(plan->copy_stream))) return cuda_fail(e, "copy stream synchronize");
+    cudaStream_t hs = h2d_stream(plan), ds = d2h_stream(plan);
+    if ((hs && (e = cudaStreamSynchronize(hs))) || (ds && (e = cudaStreamSynchronize(ds))))
+        return cuda_fail(e, "copy stream synchronize");
     if ((e = cudaStreamSynchronize(plan->stream))) return cuda_fail(e, "stream synchronize");
     int st = 0;
     if (plan->d_status) {

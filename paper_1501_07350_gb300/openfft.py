@@ -44,7 +44,7 @@ EXPORTS = [
     "openfft_mlp_num_params", "openfft_mlp_predict", "openfft_mlp_loss_grad", "openfft_mlp_train",
     "openfft_num_features", "openfft_candidate_features", "openfft_tune_times", "openfft_set_cost_model",
     "openfft_tc_gemm", "openfft_exec_r2c", "openfft_exec_c2r", "openfft_tc_debug", "openfft_set_host_chunks",
-    "openfft_exec_c2c_host_async",
+    "openfft_exec_c2c_host_async", "openfft_set_copy_streams",
 ]
 
 _lock = threading.Lock()
@@ -85,6 +85,7 @@ def load():
             "openfft_exec_c2c_host": (i32, [vp, vp, vp, i32]),
             "openfft_set_host_chunks": (i32, [vp, i32]),
             "openfft_exec_c2c_host_async": (i32, [vp, vp, vp, i32]),
+            "openfft_set_copy_streams": (i32, [vp, vp, vp]),
             "openfft_destroy": (None, [vp]),
             "openfft_sync": (i32, [vp]),
             "openfft_set_stream": (i32, [vp, vp]),
@@ -175,6 +176,14 @@ def openfft_exec_c2c_host(plan: int, host_in: np.ndarray, host_out: np.ndarray, 
 def openfft_exec_c2c_host_async(plan: int, host_in: np.ndarray, host_out: np.ndarray, direction: int) -> None:
     """Enqueue only; the buffers belong to the call until openfft_sync(plan)."""
     _check(load().openfft_exec_c2c_host_async(plan, host_in.ctypes.data, host_out.ctypes.data, direction))
+
+
+def openfft_set_copy_streams(plan: int, h2d=None, d2h=None) -> None:
+    """Upload / download streams of the host-buffer calls (torch streams, raw
+    handles or None for the plan's own)."""
+    def handle(s):
+        return None if s is None else (s.cuda_stream if hasattr(s, "cuda_stream") else s)
+    _check(load().openfft_set_copy_streams(plan, handle(h2d), handle(d2h)))
 
 
 def openfft_set_host_chunks(plan: int, chunks: int) -> None:

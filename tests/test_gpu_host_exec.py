@@ -119,18 +119,23 @@ def test_host_chunks_errors(torch):
         of.openfft_destroy(rplan)
 
 
-def test_async_host_exec_across_plans(torch):
+@pytest.mark.parametrize("shared_copy_streams", [False, True])
+def test_async_host_exec_across_plans(torch, shared_copy_streams):
     """Asynchronous host-buffer calls on three plans, enqueued back to back and
     then synchronised, give the synchronous results bit for bit, forward and
-    backward; two calls queued on one plan run in order."""
+    backward, with each plan's own copy streams or with one upload and one
+    download stream shared by all three; calls queued on one plan run in order."""
     Na, Nb, Nc = 40, 36, 48
     x = synth.complex_field((Na, Nb, Nc), seed=81).reshape(-1)
     hx = torch.from_numpy(x.copy()).pin_memory()
     plans = [of.openfft_plan(Na, Nb, Nc, P, of.C2C_F64) for P in (4, 12, 60)]
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
     try:
         for h in plans:
             of.openfft_set_stream(h, torch.cuda.current_stream())
             of.openfft_set_host_chunks(h, 5)
+            if shared_copy_streams:
+                of.openfft_set_copy_streams(h, up, down)
         want_f = [_device(torch, h, x, of.FORWARD) for h in plans]
         ys = [torch.empty_like(hx).pin_memory() for _ in plans]
         zs = [torch.empty_like(hx).pin_memory() for _ in plans]
@@ -162,3 +167,22 @@ def test_async_host_exec_across_plans(torch):
     finally:
         for h in plans:
             of.openfft_destroy(h)
+
+
+def test_copy_streams_errors_and_reset(torch):
+    plan = of.openfft_plan(8, 8, 8, 2, of.C2C_F64)
+    s = torch.cuda.Stream()
+    try:
+        for h2d, d2h in ((s, None), (None, s)):
+            with pytest.raises(of.OpenFFTError) as ei:
+                of.openfft_set_copy_streams(plan, h2d, d2h)
+            assert ei.value.status == of.ERR_INVALID_ARG
+        x = synth.complex_field((8, 8, 8), seed=3).reshape(-1)
+        want = _device(torch, plan, x, of.FORWARD)
+        for streams in ((s, s), (None, None)):          # one stream for both; back to the plan's own
+            of.openfft_set_copy_streams(plan, *streams)
+            y = np.empty_like(x)
+            of.openfft_exec_c2c_host(plan, x, y, of.FORWARD)
+            assert np.array_equal(_bits(y), _bits(want))
+    finally:
+        of.openfft_destroy(plan)
