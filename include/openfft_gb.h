@@ -180,7 +180,9 @@ int openfft_exec_c2c_host(openfft_plan_t plan, const void* host_in, void* host_o
  * stream and its stream).  Successive calls on one plan run in order.  Calls
  * on different plans may overlap their copies: the host-to-device copy of one
  * plan can run beside the device-to-host copy of another.  Same results, bit
- * for bit, as the synchronous call. */
+ * for bit, as the synchronous call.  Call openfft_sync before switching the
+ * plan to another stream (openfft_set_stream), since openfft_sync waits on the
+ * current one. */
 int openfft_exec_c2c_host_async(openfft_plan_t plan, const void* host_in, void* host_out, int dir);
 
 /* Streams of the host-buffer calls' copies: uploads on `h2d`, downloads on
