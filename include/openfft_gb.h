@@ -26,7 +26,9 @@
  * doubles for OPENFFT_C2C_F64, complex64 = two floats otherwise), 16-byte
  * aligned.  Out of place only; `in` is not modified.  The plan owns all
  * workspace, allocated once by openfft_plan (the paper moves buffer
- * allocation out of the execution phase, Sec. 3.2.4); exec allocates nothing.
+ * allocation out of the execution phase, Sec. 3.2.4); openfft_exec_c2c
+ * allocates nothing.  The host-buffer calls allocate their two staging arrays
+ * (and streams) on a plan's first host-buffer call.
  *
  * Errors.  Functions returning int return an OPENFFT_* status (0 = OK).
  * openfft_plan returns NULL on error.  openfft_last_error() gives a message
@@ -65,7 +67,7 @@ enum {
     OPENFFT_ERR_P_TOO_LARGE = 2,       /* P > N1*N2 for some ordering: Eq. 2 is undefined  */
     OPENFFT_ERR_UNSUPPORTED_RADIX = 3, /* an axis length with a prime factor other than 2,3,5,7 or above 2048 */
     OPENFFT_ERR_CUDA = 4,              /* a CUDA runtime call failed                        */
-    OPENFFT_ERR_NOMEM = 5,             /* device allocation failed at plan time             */
+    OPENFFT_ERR_NOMEM = 5,             /* device allocation failed (plan time, or the first host-buffer call) */
     OPENFFT_ERR_TIMEOUT = 6,           /* a bounded device wait ran out (batched kernel)    */
     OPENFFT_ERR_ALIAS = 7,             /* in == out                                         */
     OPENFFT_ERR_UNSUPPORTED = 8        /* the request is valid but this build does not do it */
@@ -163,13 +165,14 @@ int openfft_exec_c2r(openfft_plan_t plan, const void* in, void* out);
 /* Same transform with HOST buffers: copies `host_in` to plan-owned device
  * memory, executes, copies the result to `host_out` and waits (complex
  * plans only; N elements of the plan's external type each way).  The copies
- * run on a plan-owned second stream in ranges of lines, so that the first
- * stage starts on each range of the input as soon as it has arrived and each
- * range of the last stage's output is copied back as soon as it is written
- * (the host link, not the transform, bounds this call).  The result is bit
- * for bit that of openfft_exec_c2c.  Page-locked host memory gives the
- * fastest copies; `host_in` may equal `host_out`.  The plan allocates its
- * two device staging arrays, the stream and its events on the first call.
+ * run on the plan's upload and download streams (openfft_set_copy_streams)
+ * in ranges of lines, so that the first stage starts on each range of the
+ * input as soon as it has arrived and each range of the last stage's output
+ * is copied back as soon as it is written (the host link, not the transform,
+ * bounds this call).  The result is bit for bit that of openfft_exec_c2c.
+ * Page-locked host memory gives the fastest copies; `host_in` may equal
+ * `host_out`.  The plan allocates its two device staging arrays, its copy
+ * streams and their events on the first call.
  * While the phase timer is on (openfft_set_timing) the copies bracket the
  * whole transform instead. */
 int openfft_exec_c2c_host(openfft_plan_t plan, const void* host_in, void* host_out, int dir);
@@ -203,7 +206,8 @@ int openfft_set_host_chunks(openfft_plan_t plan, int chunks);
 /* Finalisation phase: frees everything the plan owns.  NULL-safe. */
 void openfft_destroy(openfft_plan_t plan);
 
-/* Waits for the plan's stream and reports device-side errors. */
+/* Waits for the plan's stream and its copy streams, and reports device-side
+ * errors. */
 int openfft_sync(openfft_plan_t plan);
 
 /* Use `stream` (a cudaStream_t; NULL = legacy default stream) for exec. */
