@@ -1,0 +1,49 @@
+"""Host-side helpers of bench.py (no GPU).
+
+- roofline.traffic comes from a committed ncu summary only while the stage
+  kernel sources hash to the value recorded beside it;
+- the dominant kernel is the (family, lines per CTA) most timed plans chose;
+- the FP32-issue roofline counts the double-float radix-pass arithmetic:
+  16 operations per complex addition, 32 per twiddle product, radix 2 / 4 / 8
+  butterflies at 16 / 32 / 54 per point;
+- the oracle baseline never plans more threads than host memory holds.
+"""
+import os
+
+import bench
+
+
+def test_profiled_traffic_follows_the_source_hash():
+    h = bench.stage_source_hash()
+    assert len(h) == 16
+    t = bench.profiled_traffic(h, "warp", 8)
+    assert t is not None and 2 * 256 ** 3 * 16 * 0.8 < t < 2 * 256 ** 3 * 16 * 1.1   # near the algorithmic bytes
+    assert bench.profiled_traffic("0" * 16, "warp", 8) is None                        # stale hash: no figure
+    assert bench.profiled_traffic(h, "warp", 5) is None                               # no such capture
+
+
+def test_dominant_kernel():
+    chosen = {16: {"kernel": 0, "lines_per_cta": 8}, 64: {"kernel": 0, "lines_per_cta": 8},
+              256: {"kernel": 2, "lines_per_cta": 4}}
+    assert bench.dominant_kernel(chosen) == ("warp", 8)
+    chosen = {16: {"kernel": 2, "lines_per_cta": 4}, 64: {"kernel": 2, "lines_per_cta": 4},
+              256: {"kernel": 0, "lines_per_cta": 8}}
+    assert bench.dominant_kernel(chosen) == ("tile", 4)
+
+
+def test_double_float_operation_count():
+    add, mul = 16.0, 32.0
+    radix4 = 8 * add / 4                               # two levels of 2 complex additions per pair
+    radix8 = (2 * 8 * add + 2 * (add + 8) + 8 * add) / 8  # two radix-4 halves, two (1 -+ i)/sqrt2 factors, 8 additions
+    assert radix4 == 32 and radix8 == 54
+    assert bench.df_ops_per_point(8) == radix8
+    assert bench.df_ops_per_point(64) == radix8 + radix8 + mul * 7 / 8
+    assert bench.df_ops_per_point(256) == radix4 + 2 * (radix8 + mul * 7 / 8) == 196
+    assert bench.df_ops_per_point(512) == radix8 + 2 * (radix8 + mul * 7 / 8)
+    assert bench.df_ops_per_point(32) == radix4 + radix8 + mul * 7 / 8
+
+
+def test_host_threads_respects_memory():
+    cores = len(os.sched_getaffinity(0))
+    assert 1 <= bench.host_threads(1) <= cores
+    assert bench.host_threads(1 << 60) == 1                     # nothing fits: still one thread
