@@ -193,9 +193,9 @@ int openfft_exec_c2c_host_async(openfft_plan_t plan, const void* host_in, void* 
  * plan creates and owns.  Plans given the same two streams queue their
  * transfers in call order across plans, so one plan's upload runs beside
  * another's download instead of sharing the link with the other uploads.
- * The caller keeps the streams alive while the plan may use them; copies
- * already queued on the previous streams are waited for first.  INVALID_ARG
- * if exactly one of the two is NULL. */
+ * The caller keeps the streams alive until the plan is destroyed or given
+ * other streams: openfft_destroy and this call wait for the copies queued on
+ * them.  INVALID_ARG if exactly one of the two is NULL. */
 int openfft_set_copy_streams(openfft_plan_t plan, void* h2d, void* d2h);
 
 /* Number of line ranges of openfft_exec_c2c_host: 1 (no overlap) to 32;
