@@ -73,11 +73,11 @@ def stage_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel_hash: str, family: str, G: int):
+def profiled_traffic(kernel_hash: str, family: str, G: int, path: str = ""):
     """DRAM bytes per stage launch of the double-float stage kernel of `family`
     with G lines per CTA, from the committed ncu summary, if it was taken on
     the current kernel sources."""
-    path = os.path.join(ROOT, "profiles", "fft_%s_kernel_df_256cubed.md" % family)
+    path = path or os.path.join(ROOT, "profiles", "fft_%s_kernel_df_256cubed.md" % family)
     vals = {}
     try:
         with open(path) as fh:

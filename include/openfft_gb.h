@@ -380,6 +380,71 @@ int openfft_batch_debug(openfft_plan_t plan, int what, long long value);
  * (value = 0 undoes it).  Nothing is in flight when a wait runs out. */
 int openfft_tc_debug(int what, long long value);
 
+/* ------------------------------------------- over several devices ----- */
+
+/* The transform over G devices (one process each), device g holding the
+ * contiguous block of logical ranks [floor(g P / G), floor((g+1) P / G)):
+ * the paper's distributed execution flow (Sec. 3.1.1, steps (1)-(6)) with
+ * the ranks of one device sharing its memory.  Because every rank's box is a
+ * contiguous slice of its ordering (Eqs. 3-4), device g holds one contiguous
+ * slice of each ordering (openfft_dist_rows).  Each transpose is one
+ * all-to-all with variable counts among the devices (the Alltoallv method of
+ * Sec. 3.2.1): the library packs (step 4) and unpacks (step 6); the caller's
+ * communication library moves the segments (step 5; NCCL send / recv on
+ * GPUs, gloo on CPUs).  Segment g -> h holds D[g][h] elements, the sum of the
+ * P x P count matrix over the two devices' ranks, in ascending source index;
+ * in g's send buffer the segments are ordered by destination device, in h's
+ * receive buffer by source device, each contiguous.  1 <= G <= P; every other
+ * argument and error is as for openfft_plan and openfft_counts
+ * (exchange 1 = abc->cab, 2 = cab->cba, -2 = cba->cab, -1 = cab->abc). */
+typedef struct openfft_dist_plan_s* openfft_dist_plan_t;
+
+/* Host only: device g's slice of `layout` (0 = abc, 1 = cab, 2 = cba): 1-D
+ * offset and element count.  Either pointer may be NULL. */
+int openfft_dist_rows(int Na, int Nb, int Nc, int P, int G, int layout, int g, int64_t* offset, int64_t* count);
+/* Host only: the G x G device count matrix of one transpose (row = sender),
+ * into the host array GxG of G*G entries. */
+int openfft_dist_counts(int Na, int Nb, int Nc, int P, int G, int exchange, int64_t* GxG);
+/* Host only: pack (step 4) / unpack (step 6) of device g on HOST buffers of
+ * elem_bytes-byte elements (any element type; values are moved, not read).
+ * pack: `src` = g's source slice (openfft_dist_rows of the source ordering),
+ * `send` = sum of g's row of the count matrix.  unpack: `recv` = sum of g's
+ * column, `dst` = g's destination slice. */
+int openfft_dist_pack_host(int Na, int Nb, int Nc, int P, int G, int exchange, int g, int elem_bytes,
+                           const void* src, void* send);
+int openfft_dist_unpack_host(int Na, int Nb, int Nc, int P, int G, int exchange, int g, int elem_bytes,
+                             const void* recv, void* dst);
+
+/* Plan of device g (the calling process's current CUDA device) for
+ * OPENFFT_C2C_F64 (double-float arithmetic, complex128 at the ends and in
+ * the exchanges between stages: 16-byte elements) or OPENFFT_C2C_F32
+ * (complex64, 8-byte elements).  Allocates the twiddle tables and the
+ * exchange tables; the caller owns every data buffer.  NULL on error. */
+openfft_dist_plan_t openfft_dist_plan(int Na, int Nb, int Nc, int P, int G, int g, int dtype);
+void openfft_dist_destroy(openfft_dist_plan_t plan);                       /* NULL-safe */
+int openfft_dist_set_stream(openfft_dist_plan_t plan, void* stream);       /* cudaStream_t */
+/* Bytes per element of the plan's buffers (16 or 8). */
+int openfft_dist_elem_bytes(openfft_dist_plan_t plan);
+/* Per-peer element counts of this device in one transpose: send_counts[h]
+ * to device h, recv_counts[g'] from device g' (host arrays of G; either may
+ * be NULL). */
+int openfft_dist_exchange_counts(openfft_dist_plan_t plan, int exchange, int64_t* send_counts,
+                                 int64_t* recv_counts);
+/* Line-local FFT stage (steps (1)-(3)) of this device's slice, DEVICE
+ * pointers, contiguous in and out (in == out allowed):
+ *   FORWARD  stage 1: c-lines of the abc slice (in: complex128 / complex64),
+ *            stage 2: b-lines of the cab slice, stage 3: a-lines of the cba
+ *            slice (out: complex128 / complex64);
+ *   BACKWARD stage 1: a-lines of cba (conjugated on entry), stage 2: b-lines
+ *            of cab, stage 3: c-lines of abc (conjugated and divided by N).
+ * Between stages the buffers hold the plan's internal format (double-float
+ * pairs for OPENFFT_C2C_F64), which pack and unpack move unchanged. */
+int openfft_dist_stage(openfft_dist_plan_t plan, int stage, int dir, const void* in, void* out);
+/* Pack (step 4) and unpack (step 6) of one transpose on DEVICE buffers of
+ * openfft_dist_elem_bytes elements, asynchronous on the plan's stream. */
+int openfft_dist_pack(openfft_dist_plan_t plan, int exchange, const void* src, void* send);
+int openfft_dist_unpack(openfft_dist_plan_t plan, int exchange, const void* recv, void* dst);
+
 /* ------------------------------------------------- allocation-free ----- */
 
 /* The same transform as openfft_exec_c2c (fused variant, default arithmetic
@@ -393,13 +458,18 @@ int openfft_tc_debug(int what, long long value);
  * for OPENFFT_C2C_F64, complex64 for OPENFFT_C2C_F32, 16-byte aligned, in !=
  * out) and a cudaStream_t `stream` (NULL = legacy default stream); P, the
  * layouts and dir are as for openfft_plan / openfft_exec_c2c.  The
- * intermediate array and twiddle tables live in a 16 MiB (+96 KiB) static
+ * intermediate array and twiddle tables live in a 16 MiB (+384 KiB) static
  * device array that every GPU loading this library keeps until the process
  * exits: N times the element size (16 or 8 bytes) must not exceed 16 MiB and
  * no axis may exceed 2048, otherwise the call returns OPENFFT_ERR_UNSUPPORTED
  * without touching the GPU.  The array's device address is looked up on the
- * first call on each device (with that device current), so make that first
- * call before any stream capture.  All calls share the array: calls whose
+ * first call on each device (with that device current) and kept, so make that
+ * first call before any stream capture.  A device reset (cudaDeviceReset) can
+ * move the array: the address is looked up again after any call on that
+ * device has returned OPENFFT_ERR_CUDA, so after a reset the first call that
+ * fails with OPENFFT_ERR_CUDA is followed by calls that work again.  Every
+ * call writes all of the array it later reads, so nothing needs clearing
+ * between calls.  All calls share the array: calls whose
  * kernels may overlap on the GPU (unordered streams) race and must be
  * serialised by the caller.  Asynchronous on `stream`. */
 int openfft_exec_c2c_noalloc(int Na, int Nb, int Nc, int P, int dtype,

@@ -24,6 +24,9 @@ struct ArF64 {
     using C = double2;
     using W = double2;
     static constexpr int kElemBytes = 16;
+    // twiddle table of a line length n (one W per exponent) and its load
+    __device__ __forceinline__ static const W* table(const void* tw, int) { return reinterpret_cast<const W*>(tw); }
+    __device__ __forceinline__ static W ldw(const W* p) { return __ldg(p); }
     __device__ __forceinline__ static C zero() { return make_double2(0.0, 0.0); }
     __device__ __forceinline__ static C add(C a, C b) { return make_double2(a.x + b.x, a.y + b.y); }
     __device__ __forceinline__ static C sub(C a, C b) { return make_double2(a.x - b.x, a.y - b.y); }
@@ -42,6 +45,9 @@ struct ArF32 {
     using C = float2;
     using W = float2;
     static constexpr int kElemBytes = 8;
+    // twiddle table of a line length n (one W per exponent) and its load
+    __device__ __forceinline__ static const W* table(const void* tw, int) { return reinterpret_cast<const W*>(tw); }
+    __device__ __forceinline__ static W ldw(const W* p) { return __ldg(p); }
     __device__ __forceinline__ static C zero() { return make_float2(0.f, 0.f); }
     __device__ __forceinline__ static C add(C a, C b) { return make_float2(a.x + b.x, a.y + b.y); }
     __device__ __forceinline__ static C sub(C a, C b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -62,6 +68,9 @@ struct ArDF {
     using C = float4;
     using W = float4;
     static constexpr int kElemBytes = 16;
+    // twiddle table of a line length n (one W per exponent) and its load
+    __device__ __forceinline__ static const W* table(const void* tw, int) { return reinterpret_cast<const W*>(tw); }
+    __device__ __forceinline__ static W ldw(const W* p) { return __ldg(p); }
 
     // Knuth TwoSum: s + e == a + b exactly.
     __device__ __forceinline__ static void two_sum(float a, float b, float& s, float& e) {

@@ -281,7 +281,7 @@ int batch_create(int count, const int* dims, const int* P, int dtype, int sms, B
     auto twiddle_for = [&](int n) -> const void* {
         for (size_t k = 0; k < tw_len.size(); ++k) if (tw_len[k] == n) return b->twiddles[k];
         void* t = nullptr;
-        if (cudaMalloc(&t, (size_t)n * (twf == FMT_C64 ? 8 : 16))) return nullptr;
+        if (cudaMalloc(&t, twiddle_bytes(n, twf))) return nullptr;
         if (launch_twiddles(n, twf, t, nullptr)) { cudaFree(t); return nullptr; }
         tw_len.push_back(n);
         b->twiddles.push_back(t);

@@ -686,8 +686,7 @@ openfft_plan_t openfft_plan(int Na, int Nb, int Nc, int P, int dtype)
         const int fmts[2] = {c64 ? FMT_C64 : FMT_C128, c64 ? -1 : FMT_DF};
         for (int f : fmts) {
             if (f < 0) continue;
-            const size_t eb = f == FMT_C64 ? 8 : 16;
-            if (cudaMalloc(&p->tw[ax][f], eb * (size_t)lens[ax])) {
+            if (cudaMalloc(&p->tw[ax][f], twiddle_bytes(lens[ax], f))) {
                 cudaGetLastError();
                 fail(OPENFFT_ERR_NOMEM, "twiddle allocation failed");
                 free_plan(p);

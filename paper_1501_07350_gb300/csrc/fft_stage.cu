@@ -45,7 +45,10 @@ fft_stage_kernel(const StageArgs p)
 
 // ---------------------------------------------------- twiddle tables ----
 
-// W[e] = exp(-2 pi i e / n), from the FP64 sincospi of 2e/n.
+// W[e] = exp(-2 pi i e / n), from the FP64 sincospi of 2e/n.  A double-float
+// table (FMT_DF) holds n float4 entries (hi and lo parts) and after them n
+// 48-byte entries of the same values arranged for the packed product
+// (arith_pair.cuh), 64 * n bytes in all.
 __global__ void twiddle_kernel(int n, int fmt, void* out)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -59,8 +62,13 @@ __global__ void twiddle_kernel(int n, int fmt, void* out)
         reinterpret_cast<float2*>(out)[e] = make_float2((float)re, (float)im);
     } else {
         const float hr = (float)re, hi = (float)im;
-        reinterpret_cast<float4*>(out)[e] =
-            make_float4(hr, hi, (float)(re - (double)hr), (float)(im - (double)hi));
+        const float lr = (float)(re - (double)hr), li = (float)(im - (double)hi);
+        reinterpret_cast<float4*>(out)[e] = make_float4(hr, hi, lr, li);
+        // then the lane pairs of the packed double-float product (ArDP::W)
+        float4* q = reinterpret_cast<float4*>(reinterpret_cast<char*>(out) + 16 * (size_t)n) + 3 * (size_t)e;
+        q[0] = make_float4(hr, hr, -hr, -hr);
+        q[1] = make_float4(-hi, hi, hi, -hi);
+        q[2] = make_float4(lr, lr, -li, li);
     }
 }
 

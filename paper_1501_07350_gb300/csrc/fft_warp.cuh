@@ -19,6 +19,7 @@
 // copied (cp.async) while the current tile is transformed.
 #pragma once
 #include "arith.cuh"
+#include "arith_pair.cuh"
 #include "fft_stage.h"
 #include "fft_tile.cuh"
 #include "stage_io.cuh"
@@ -90,7 +91,7 @@ struct WarpLine {
                     const int ks = k * s;
 #pragma unroll
                     for (int j = 1; j < R; ++j) {
-                        const W w = __ldg(tw + j * ks);
+                        const W w = A::ldw(tw + j * ks);
 #pragma unroll
                         for (int i = 0; i < L; ++i) v[i][u][j] = A::mul(v[i][u][j], w);
                     }
@@ -250,7 +251,7 @@ fft_warp_kernel(const StageArgs p, int64_t ntiles)
     C* nxt = DB ? cur + G * LS : cur;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g0 = warp * L;                // this warp's first line of the tile
-    const typename A::W* tw = reinterpret_cast<const typename A::W*>(p.tw);
+    const typename A::W* tw = A::table(p.tw, N);
     const bool convert = Io<A>::kConverts && p.in_fmt == FMT_C128;
 
     int64_t tile = blockIdx.x;

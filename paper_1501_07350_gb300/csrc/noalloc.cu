@@ -34,7 +34,8 @@ namespace {
 
 constexpr size_t kScratchBytes = 16u << 20;                // intermediate array (16 MiB)
 constexpr int kNoallocMaxLen = 2048;                       // longest axis
-constexpr size_t kTwiddleBytes = 3 * (size_t)kNoallocMaxLen * 16;   // three axis tables
+constexpr size_t kTwiddleSlot = (size_t)kNoallocMaxLen * 64;        // largest table (FMT_DF)
+constexpr size_t kTwiddleBytes = 3 * kTwiddleSlot;                    // three axis tables
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes + kTwiddleBytes];
 
@@ -42,7 +43,11 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (looked up once).
+// Device address of the scratch array on the current device, looked up on the
+// first call on that device and cached.  A device reset (cudaDeviceReset, or a
+// context torn down and created again) can move the array: the cache entry is
+// dropped whenever a call on that device meets a CUDA error, and
+// forget_scratch_address() drops it explicitly.
 int scratch_address(void** out)
 {
     int dev = 0;
@@ -59,6 +64,20 @@ int scratch_address(void** out)
     }
     *out = g_scratch_ptr[dev];
     return OPENFFT_OK;
+}
+
+void forget_scratch_address()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_scratch_ptr[dev] = nullptr;
+}
+
+int cuda_fail(cudaError_t e)
+{
+    forget_scratch_address();
+    return set_last_error(OPENFFT_ERR_CUDA, cudaGetErrorString(e));
 }
 
 bool radix_plan(int n, StageArgs& a)
@@ -88,6 +107,9 @@ int stage(int n, int arith, const void* tw, int sms, int64_t M1, int64_t M2, int
     const int64_t Mg = group_i2 ? M2 : M1;
     while (G > 1 && (int64_t)(G / 2) >= Mg) G /= 2;
     while (G > 1 && 2 * (size_t)n * (G + 1) * E > 200 * 1024) G /= 2;
+    // the same final checks as the plan path: two tiles of G lines must fit in
+    // shared memory, and the grid in a launch
+    if (2 * (size_t)n * (G + 1) * E > 200 * 1024) return set_last_error(OPENFFT_ERR_UNSUPPORTED_RADIX, "axis too long for one CTA");
     int lg = 0;
     while ((1 << lg) < G) ++lg;
     a.tw = tw;
@@ -103,6 +125,7 @@ int stage(int n, int arith, const void* tw, int sms, int64_t M1, int64_t M2, int
     L.smem = 2 * (size_t)n * (G + 1) * E;
     L.sms = sms;
     L.family = KERNEL_AUTO;
+    if (L.grid > 0x7fffffffLL) return set_last_error(OPENFFT_ERR_UNSUPPORTED, "grid too large");
     return OPENFFT_OK;
 }
 
@@ -134,15 +157,15 @@ extern "C" int openfft_exec_c2c_noalloc(int Na, int Nb, int Nc, int P, int dtype
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e = stage_kernels_init(200 * 1024);
-    if (e) return set_last_error(OPENFFT_ERR_CUDA, cudaGetErrorString(e));
+    if (e) return cuda_fail(e);
 
     unsigned char* scratch = static_cast<unsigned char*>(base);
     unsigned char* twb = scratch + kScratchBytes;
-    void* tw[3] = {twb, twb + (size_t)kNoallocMaxLen * 16, twb + 2 * (size_t)kNoallocMaxLen * 16};
+    void* tw[3] = {twb, twb + kTwiddleSlot, twb + 2 * kTwiddleSlot};
     const int lens[3] = {Na, Nb, Nc};
     const int twf = arith == ARITH_F32 ? FMT_C64 : FMT_DF;
     for (int ax = 0; ax < 3; ++ax)
-        if ((e = launch_twiddles(lens[ax], twf, tw[ax], s))) return set_last_error(OPENFFT_ERR_CUDA, cudaGetErrorString(e));
+        if ((e = launch_twiddles(lens[ax], twf, tw[ax], s))) return cuda_fail(e);
 
     const int ext = arith == ARITH_F32 ? FMT_C64 : FMT_C128;
     const int mid = arith == ARITH_F32 ? FMT_C64 : FMT_DF;
@@ -160,6 +183,6 @@ extern "C" int openfft_exec_c2c_noalloc(int Na, int Nb, int Nc, int P, int dtype
     L[1].args.in = scratch; L[1].args.out = out;
     L[2].args.in = out;     L[2].args.out = out;
     for (int i = 0; i < 3; ++i)
-        if ((e = launch_stage(L[i], s))) return set_last_error(OPENFFT_ERR_CUDA, cudaGetErrorString(e));
+        if ((e = launch_stage(L[i], s))) return cuda_fail(e);
     return OPENFFT_OK;
 }

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "arith.cuh"
+#include "arith_pair.cuh"
 #include "fft_stage.h"
 
 namespace ofg {
@@ -121,6 +122,21 @@ template <> struct Io<ArDF> {
     __device__ __forceinline__ static void store(void* p, int fmt, int64_t i, float4 v) {
         if (fmt == FMT_DF) reinterpret_cast<float4*>(p)[i] = v;
         else reinterpret_cast<double2*>(p)[i] = df_to_double2(v);
+    }
+};
+
+// The paired double-float policy has ArDF's bytes in ArDF's order.
+template <> struct Io<ArDP> {
+    static constexpr bool kConverts = true;
+    static constexpr int kExtBytes = 16, kMidBytes = 16;
+    __device__ __forceinline__ static void store_ext(void* p, ulonglong2 v) { *reinterpret_cast<double2*>(p) = df_to_double2(ArDP::to_float4(v)); }
+    __device__ __forceinline__ static void store_mid(void* p, ulonglong2 v) { *reinterpret_cast<ulonglong2*>(p) = v; }
+    __device__ __forceinline__ static ulonglong2 from_c128(double2 v) { return ArDP::from_float4(df_from_double2(v)); }
+    __device__ __forceinline__ static ulonglong2 load(const void* p, int fmt, int64_t i) {
+        return ArDP::from_float4(Io<ArDF>::load(p, fmt, i));
+    }
+    __device__ __forceinline__ static void store(void* p, int fmt, int64_t i, ulonglong2 v) {
+        Io<ArDF>::store(p, fmt, i, ArDP::to_float4(v));
     }
 };
 

@@ -45,6 +45,9 @@ EXPORTS = [
     "openfft_num_features", "openfft_candidate_features", "openfft_tune_times", "openfft_set_cost_model",
     "openfft_tc_gemm", "openfft_exec_r2c", "openfft_exec_c2r", "openfft_tc_debug", "openfft_set_host_chunks",
     "openfft_exec_c2c_host_async", "openfft_set_copy_streams",
+    "openfft_dist_rows", "openfft_dist_counts", "openfft_dist_pack_host", "openfft_dist_unpack_host",
+    "openfft_dist_plan", "openfft_dist_destroy", "openfft_dist_set_stream", "openfft_dist_elem_bytes",
+    "openfft_dist_exchange_counts", "openfft_dist_stage", "openfft_dist_pack", "openfft_dist_unpack",
 ]
 
 _lock = threading.Lock()
@@ -116,6 +119,18 @@ def load():
             "openfft_tune_times": (i32, [vp, pf]),
             "openfft_set_cost_model": (i32, [i32, i32, i32, pf]),
             "openfft_tc_gemm": (i32, [i32, i32, i32, i32, i32, pf, pf, pf]),
+            "openfft_dist_rows": (i32, [i32, i32, i32, i32, i32, i32, i32, p64, p64]),
+            "openfft_dist_counts": (i32, [i32, i32, i32, i32, i32, i32, p64]),
+            "openfft_dist_pack_host": (i32, [i32, i32, i32, i32, i32, i32, i32, i32, vp, vp]),
+            "openfft_dist_unpack_host": (i32, [i32, i32, i32, i32, i32, i32, i32, i32, vp, vp]),
+            "openfft_dist_plan": (vp, [i32, i32, i32, i32, i32, i32, i32]),
+            "openfft_dist_destroy": (None, [vp]),
+            "openfft_dist_set_stream": (i32, [vp, vp]),
+            "openfft_dist_elem_bytes": (i32, [vp]),
+            "openfft_dist_exchange_counts": (i32, [vp, i32, p64, p64]),
+            "openfft_dist_stage": (i32, [vp, i32, i32, vp, vp]),
+            "openfft_dist_pack": (i32, [vp, i32, vp, vp]),
+            "openfft_dist_unpack": (i32, [vp, i32, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -279,6 +294,74 @@ def openfft_exec_c2c_noalloc(Na: int, Nb: int, Nc: int, P: int, dtype: int, inp,
     """Plan-free transform that allocates nothing (static device scratch, 16 MiB)."""
     raw = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     _check(load().openfft_exec_c2c_noalloc(Na, Nb, Nc, P, dtype, _ptr(inp), _ptr(out), direction, raw))
+
+
+# ------------------------------------------- transform over several devices --
+
+def openfft_dist_rows(Na, Nb, Nc, P, G, layout, g):
+    """(offset, count) of device g's slice of `layout` (host only)."""
+    off, cnt = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().openfft_dist_rows(Na, Nb, Nc, P, G, layout, g, ctypes.byref(off), ctypes.byref(cnt)))
+    return off.value, cnt.value
+
+
+def openfft_dist_counts(Na, Nb, Nc, P, G, exchange) -> np.ndarray:
+    """G x G device count matrix of one transpose (host only)."""
+    out = np.zeros((G, G), dtype=np.int64)
+    _check(load().openfft_dist_counts(Na, Nb, Nc, P, G, exchange,
+                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return out
+
+
+def openfft_dist_pack_host(Na, Nb, Nc, P, G, exchange, g, src: np.ndarray, send: np.ndarray) -> None:
+    _check(load().openfft_dist_pack_host(Na, Nb, Nc, P, G, exchange, g, src.itemsize,
+                                         src.ctypes.data, send.ctypes.data))
+
+
+def openfft_dist_unpack_host(Na, Nb, Nc, P, G, exchange, g, recv: np.ndarray, dst: np.ndarray) -> None:
+    _check(load().openfft_dist_unpack_host(Na, Nb, Nc, P, G, exchange, g, recv.itemsize,
+                                           recv.ctypes.data, dst.ctypes.data))
+
+
+def openfft_dist_plan(Na, Nb, Nc, P, G, g, dtype) -> int:
+    h = load().openfft_dist_plan(Na, Nb, Nc, P, G, g, dtype)
+    if not h:
+        raise OpenFFTError(load().openfft_last_status(), last_error())
+    return h
+
+
+def openfft_dist_destroy(plan: int) -> None:
+    load().openfft_dist_destroy(plan)
+
+
+def openfft_dist_set_stream(plan: int, stream) -> None:
+    raw = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(load().openfft_dist_set_stream(plan, raw))
+
+
+def openfft_dist_elem_bytes(plan: int) -> int:
+    return int(load().openfft_dist_elem_bytes(plan))
+
+
+def openfft_dist_exchange_counts(plan: int, exchange: int, G: int):
+    """(send_counts[G], recv_counts[G]) of this device in one transpose."""
+    sc = np.zeros(G, dtype=np.int64)
+    rc = np.zeros(G, dtype=np.int64)
+    p64 = ctypes.POINTER(ctypes.c_int64)
+    _check(load().openfft_dist_exchange_counts(plan, exchange, sc.ctypes.data_as(p64), rc.ctypes.data_as(p64)))
+    return sc, rc
+
+
+def openfft_dist_stage(plan: int, stage: int, direction: int, inp, out) -> None:
+    _check(load().openfft_dist_stage(plan, stage, direction, _ptr(inp), _ptr(out)))
+
+
+def openfft_dist_pack(plan: int, exchange: int, src, send) -> None:
+    _check(load().openfft_dist_pack(plan, exchange, _ptr(src), _ptr(send)))
+
+
+def openfft_dist_unpack(plan: int, exchange: int, recv, dst) -> None:
+    _check(load().openfft_dist_unpack(plan, exchange, _ptr(recv), _ptr(dst)))
 
 
 def openfft_plan_many(shapes, Ps, dtype: int) -> int:

@@ -13,13 +13,15 @@ import os
 import bench
 
 
-def test_profiled_traffic_follows_the_source_hash():
+def test_profiled_traffic_follows_the_source_hash(tmp_path):
     h = bench.stage_source_hash()
     assert len(h) == 16
-    t = bench.profiled_traffic(h, "warp", 8)
-    assert t is not None and 2 * 256 ** 3 * 16 * 0.8 < t < 2 * 256 ** 3 * 16 * 1.1   # near the algorithmic bytes
-    assert bench.profiled_traffic("0" * 16, "warp", 8) is None                        # stale hash: no figure
-    assert bench.profiled_traffic(h, "warp", 5) is None                               # no such capture
+    summary = tmp_path / "summary.md"
+    summary.write_text("text\n\n    source_hash: %s\n    dram_bytes_per_launch G8: 484393045\n" % h)
+    assert bench.profiled_traffic(h, "warp", 8, str(summary)) == 484393045.0
+    assert bench.profiled_traffic("0" * 16, "warp", 8, str(summary)) is None          # stale hash: no figure
+    assert bench.profiled_traffic(h, "warp", 5, str(summary)) is None                 # no such capture
+    assert bench.profiled_traffic(h, "warp", 8, str(tmp_path / "absent.md")) is None
 
 
 def test_dominant_kernel():
