@@ -27,6 +27,10 @@ struct ArF64 {
     // twiddle table of a line length n (one W per exponent) and its load
     __device__ __forceinline__ static const W* table(const void* tw, int) { return reinterpret_cast<const W*>(tw); }
     __device__ __forceinline__ static W ldw(const W* p) { return __ldg(p); }
+    // twiddle W_N^(j ks) of a warp-kernel pass (the per-pass arguments are
+    // for policies with per-pass tables)
+    template <int N>
+    __device__ __forceinline__ static W warp_twiddle(const W* tw, int, int, int j, int, int ks) { return __ldg(tw + j * ks); }
     __device__ __forceinline__ static C zero() { return make_double2(0.0, 0.0); }
     __device__ __forceinline__ static C add(C a, C b) { return make_double2(a.x + b.x, a.y + b.y); }
     __device__ __forceinline__ static C sub(C a, C b) { return make_double2(a.x - b.x, a.y - b.y); }
@@ -48,6 +52,10 @@ struct ArF32 {
     // twiddle table of a line length n (one W per exponent) and its load
     __device__ __forceinline__ static const W* table(const void* tw, int) { return reinterpret_cast<const W*>(tw); }
     __device__ __forceinline__ static W ldw(const W* p) { return __ldg(p); }
+    // twiddle W_N^(j ks) of a warp-kernel pass (the per-pass arguments are
+    // for policies with per-pass tables)
+    template <int N>
+    __device__ __forceinline__ static W warp_twiddle(const W* tw, int, int, int j, int, int ks) { return __ldg(tw + j * ks); }
     __device__ __forceinline__ static C zero() { return make_float2(0.f, 0.f); }
     __device__ __forceinline__ static C add(C a, C b) { return make_float2(a.x + b.x, a.y + b.y); }
     __device__ __forceinline__ static C sub(C a, C b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -71,6 +79,10 @@ struct ArDF {
     // twiddle table of a line length n (one W per exponent) and its load
     __device__ __forceinline__ static const W* table(const void* tw, int) { return reinterpret_cast<const W*>(tw); }
     __device__ __forceinline__ static W ldw(const W* p) { return __ldg(p); }
+    // twiddle W_N^(j ks) of a warp-kernel pass (the per-pass arguments are
+    // for policies with per-pass tables)
+    template <int N>
+    __device__ __forceinline__ static W warp_twiddle(const W* tw, int, int, int j, int, int ks) { return __ldg(tw + j * ks); }
 
     // Knuth TwoSum: s + e == a + b exactly.
     __device__ __forceinline__ static void two_sum(float a, float b, float& s, float& e) {

@@ -16,10 +16,10 @@
 // bit those of ArDF.  The twiddle product computes the same terms; only the
 // order of the four first-order terms of the imaginary lo part differs.
 //
-// There is no packed negation: a product's rounding error e = fma(a, b, -p)
-// is formed as -e = fma(a, -b, p) with the negated factor taken from the
-// twiddle table (or a negated constant), and the sign folded into the next
-// addition.  Multiplication by -i swaps the lanes of a pair, which costs
+// There is no packed negation: a twiddle product's rounding error
+// e = fma(a, b, -p) is formed as -e = fma(a, -b, p) with the negated factor
+// taken from the twiddle table and the sign folded into the next addition;
+// a scaling by a constant negates p by its sign bits.  Multiplication by -i swaps the lanes of a pair, which costs
 // register moves, so the radix-4 and radix-8 butterflies fuse it into the
 // addition that consumes it (add_mi / sub_mi, lane signs through fma by
 // (+1, -1)).
@@ -80,6 +80,7 @@ __device__ __forceinline__ u64 p2_splat(float x) { return p2_pack(x, x); }
 constexpr u64 kSgnPM = 0xBF8000003F800000ull;   // (+1, -1)
 constexpr u64 kSgnMP = 0x3F800000BF800000ull;   // (-1, +1)
 constexpr u64 kSignHi = 0x8000000000000000ull;  // sign bit of the high lane
+constexpr u64 kSignBoth = 0x8000000080000000ull;  // sign bits of both lanes
 
 struct ArDP {
     using C = ulonglong2;                 // x = (re.hi, im.hi), y = (re.lo, im.lo)
@@ -90,18 +91,23 @@ struct ArDP {
     struct W { ulonglong2 a, b, c; };
     static constexpr int kElemBytes = 16;
 
-    // The FMT_DF twiddle table holds n float4 entries (ArDF) followed by n
-    // entries of this form.
+    // The FMT_DF twiddle table of a power-of-two length n <= 512 holds n
+    // float4 entries (ArDF) followed by three arrays of n 16-byte slots: the
+    // components a, b and c of the per-pass tables of the warp kernel's radix
+    // plan (warp_plan.h).  table() points at array a.
     __device__ __forceinline__ static const W* table(const void* tw, int n)
     {
         return reinterpret_cast<const W*>(reinterpret_cast<const char*>(tw) + 16 * (size_t)n);
     }
-    __device__ __forceinline__ static W ldw(const W* p)
+    template <int N>
+    __device__ __forceinline__ static W warp_twiddle(const W* tw, int off, int m, int j, int k, int)
     {
+        const ulonglong2* a = reinterpret_cast<const ulonglong2*>(tw);
+        const int e = off + (j - 1) * m + k;
         W w;
-        w.a = __ldg(&p->a);
-        w.b = __ldg(&p->b);
-        w.c = __ldg(&p->c);
+        w.a = __ldg(a + e);
+        w.b = __ldg(a + N + e);
+        w.c = __ldg(a + 2 * N + e);
         return w;
     }
 
@@ -174,15 +180,17 @@ struct ArDP {
         l = p2_fma(als, w.b.x, l);
         return make(s, l);
     }
-    // multiply by the real constant k = kh + kl
+    // multiply by the real constant k = kh + kl.  The product's rounding
+    // error is fma(a, kh, -p) with -p formed by flipping both sign bits: with
+    // -p formed as a product by the negated constant, ptxas (-O1 and above)
+    // was seen to lose the error term.
     __device__ __forceinline__ static C scale(C a, double k)
     {
         const float kh = (float)k;
         const float kl = (float)(k - (double)kh);
-        const u64 KH = p2_splat(kh), KHn = p2_splat(-kh), KL = p2_splat(kl);
+        const u64 KH = p2_splat(kh), KL = p2_splat(kl);
         const u64 p = p2_mul(a.x, KH);
-        const u64 pn = p2_mul(a.x, KHn);
-        u64 e = p2_fma(a.x, KH, pn);
+        u64 e = p2_fma(a.x, KH, p ^ kSignBoth);
         e = p2_fma(a.x, KL, e);
         e = p2_fma(a.y, KH, e);
         return make(p, e);

@@ -30,6 +30,7 @@
 #include "arith.cuh"
 #include "stage_io.cuh"
 #include "generic_stage.cuh"
+#include "warp_plan.h"
 
 namespace ofg {
 
@@ -46,9 +47,8 @@ fft_stage_kernel(const StageArgs p)
 // ---------------------------------------------------- twiddle tables ----
 
 // W[e] = exp(-2 pi i e / n), from the FP64 sincospi of 2e/n.  A double-float
-// table (FMT_DF) holds n float4 entries (hi and lo parts) and after them n
-// 48-byte entries of the same values arranged for the packed product
-// (arith_pair.cuh), 64 * n bytes in all.
+// table (FMT_DF) holds n float4 entries (hi and lo parts), followed by the
+// per-pass tables of the packed product (warp_twiddle_kernel): 64 n bytes.
 __global__ void twiddle_kernel(int n, int fmt, void* out)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -64,12 +64,32 @@ __global__ void twiddle_kernel(int n, int fmt, void* out)
         const float hr = (float)re, hi = (float)im;
         const float lr = (float)(re - (double)hr), li = (float)(im - (double)hi);
         reinterpret_cast<float4*>(out)[e] = make_float4(hr, hi, lr, li);
-        // then the lane pairs of the packed double-float product (ArDP::W)
-        float4* q = reinterpret_cast<float4*>(reinterpret_cast<char*>(out) + 16 * (size_t)n) + 3 * (size_t)e;
-        q[0] = make_float4(hr, hr, -hr, -hr);
-        q[1] = make_float4(-hi, hi, hi, -hi);
-        q[2] = make_float4(lr, lr, -li, li);
     }
+}
+
+// The per-pass twiddle tables of the warp kernel's radix plan for the packed
+// double-float product (arith_pair.cuh, warp_plan.h): entry e of pass p is
+// W_n^(j k s_p), stored as three 16-byte components in arrays of n slots
+// after the n float4 entries of the FMT_DF table.
+__global__ void warp_twiddle_kernel(int n, void* out)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= wtw_count(n)) return;
+    int p = 1;
+    while (p + 1 < wplan_len(n) && e >= wtw_offset(n, p + 1)) ++p;
+    const int m = wplan_m(n, p), R = wplan_radix(n, p);
+    const int s = n / (m * R);
+    const int j = (e - wtw_offset(n, p)) / m + 1, k = (e - wtw_offset(n, p)) % m;
+    const int ex = (int)(((int64_t)j * k * s) % n);
+    double sn, c;
+    sincospi((double)(2 * (int64_t)ex) / (double)n, &sn, &c);
+    const double re = c, im = -sn;
+    const float hr = (float)re, hi = (float)im;
+    const float lr = (float)(re - (double)hr), li = (float)(im - (double)hi);
+    float4* a = reinterpret_cast<float4*>(reinterpret_cast<char*>(out) + 16 * (size_t)n);
+    a[e] = make_float4(hr, hr, -hr, -hr);              // t0, -t0
+    a[n + e] = make_float4(-hi, hi, hi, -hi);          // t1 = (-im, im), -t1
+    a[2 * n + e] = make_float4(lr, lr, -li, li);       // t2 = (lo re, lo re), t3 = (-lo im, lo im)
 }
 
 // --------------------------------------------------------- host side ----
@@ -141,6 +161,7 @@ cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st)
 cudaError_t launch_twiddles(int n, int fmt, void* out, cudaStream_t st)
 {
     twiddle_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, fmt, out);
+    if (fmt == FMT_DF && warp_length(n)) warp_twiddle_kernel<<<(wtw_count(n) + 255) / 256, 256, 0, st>>>(n, out);
     return cudaGetLastError();
 }
 

@@ -1,5 +1,6 @@
 // fft_tile_df.cu -- instantiations of the specialised stage kernels for one arithmetic:
 // warp-per-line kernels for power-of-two lengths, tile kernels for the others.
+// The double-float warp kernels run the packed-lane policy (arith_pair.cuh).
 #include "fft_tile.cuh"
 #include "fft_warp.cuh"
 
@@ -9,7 +10,7 @@ cudaError_t launch_tile_df(const StageLaunch& L, cudaStream_t st, bool* handled)
 {
     *handled = false;
     if ((L.family == KERNEL_AUTO || L.family == KERNEL_WARP) && (L.args.G == 4 || L.args.G == 8)) {
-        cudaError_t e = L.args.G == 4 ? launch_warp_g<ArDF, 4>(L, st, handled) : launch_warp_g<ArDF, 8>(L, st, handled);
+        cudaError_t e = L.args.G == 4 ? launch_warp_g<ArDP, 4>(L, st, handled) : launch_warp_g<ArDP, 8>(L, st, handled);
         if (*handled || e) return e;
     }
     if (L.family == KERNEL_WARP) return cudaSuccess;

@@ -23,31 +23,9 @@
 #include "fft_stage.h"
 #include "fft_tile.cuh"
 #include "stage_io.cuh"
+#include "warp_plan.h"
 
 namespace ofg {
-
-constexpr int wplan_len(int n)
-{
-    int c = 0;
-    while (n % 8 == 0) { n /= 8; ++c; }
-    return c + (n > 1 ? 1 : 0);
-}
-
-// remainder radix (N / 8^k, which is 1, 2 or 4) first, then radix 8
-constexpr int wplan_radix(int n, int idx)
-{
-    int k = 0, r = n;
-    while (r % 8 == 0) { r /= 8; ++k; }
-    if (r > 1) return idx == 0 ? r : 8;
-    return 8;
-}
-
-constexpr int wplan_m(int n, int idx)
-{
-    int m = 1;
-    for (int i = 0; i < idx; ++i) m *= wplan_radix(n, i);
-    return m;
-}
 
 // one padding element per 128 bytes of line: per 8 elements of 16 bytes,
 // per 16 elements of 8 bytes
@@ -91,7 +69,7 @@ struct WarpLine {
                     const int ks = k * s;
 #pragma unroll
                     for (int j = 1; j < R; ++j) {
-                        const W w = A::ldw(tw + j * ks);
+                        const W w = A::template warp_twiddle<N>(tw, wtw_offset(N, P), m, j, k, ks);
 #pragma unroll
                         for (int i = 0; i < L; ++i) v[i][u][j] = A::mul(v[i][u][j], w);
                     }

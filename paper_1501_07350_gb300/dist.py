@@ -92,15 +92,25 @@ class DistFFT:
                                group=self.group)
         return recv
 
-    def transpose(self, exchange: int, src):
-        """One transpose of this device's slice (steps (4)-(6))."""
+    def pack(self, exchange: int, src):
+        """Step (4): the send buffer of this device, segments by destination."""
         import torch
         send = torch.empty(sum(self.send_counts[exchange]), dtype=src.dtype, device=src.device)
         self.ops.pack(exchange, src, send)
-        recv = self._exchange(send, self.send_counts[exchange], self.recv_counts[exchange])
-        dst = torch.empty(sum(self.recv_counts[exchange]), dtype=src.dtype, device=src.device)
+        return send
+
+    def unpack(self, exchange: int, recv):
+        """Step (6): this device's slice of the destination ordering."""
+        import torch
+        dst = torch.empty(sum(self.recv_counts[exchange]), dtype=recv.dtype, device=recv.device)
         self.ops.unpack(exchange, recv, dst)
         return dst
+
+    def transpose(self, exchange: int, src):
+        """One transpose of this device's slice (steps (4)-(6))."""
+        send = self.pack(exchange, src)
+        recv = self._exchange(send, self.send_counts[exchange], self.recv_counts[exchange])
+        return self.unpack(exchange, recv)
 
     def forward(self, x):
         """abc slice -> cba slice (unnormalised, exp(-2 pi i ...))."""

@@ -17,11 +17,11 @@ def test_profiled_traffic_follows_the_source_hash(tmp_path):
     h = bench.stage_source_hash()
     assert len(h) == 16
     summary = tmp_path / "summary.md"
-    summary.write_text("text\n\n    source_hash: %s\n    dram_bytes_per_launch G8: 484393045\n" % h)
-    assert bench.profiled_traffic(h, "warp", 8, str(summary)) == 484393045.0
-    assert bench.profiled_traffic("0" * 16, "warp", 8, str(summary)) is None          # stale hash: no figure
-    assert bench.profiled_traffic(h, "warp", 5, str(summary)) is None                 # no such capture
-    assert bench.profiled_traffic(h, "warp", 8, str(tmp_path / "absent.md")) is None
+    summary.write_text("text\n\n    source_hash: %s\n    dram_bytes_per_point G8: 29.5\n" % h)
+    assert bench.profiled_traffic(h, "warp", 8, 512, str(summary)) == 29.5
+    assert bench.profiled_traffic("0" * 16, "warp", 8, 512, str(summary)) is None     # stale hash: no figure
+    assert bench.profiled_traffic(h, "warp", 5, 512, str(summary)) is None            # no such capture
+    assert bench.profiled_traffic(h, "warp", 8, 512, str(tmp_path / "absent.md")) is None
 
 
 def test_dominant_kernel():
