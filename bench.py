@@ -69,8 +69,9 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-STAGE_SOURCES = ("fft_warp.cuh", "fft_tile.cuh", "stage_io.cuh", "arith.cuh", "arith_pair.cuh", "warp_plan.h",
-                 "fft_stage.h", "generic_stage.cuh", "fft_stage.cu", "fft_tile_df.cu")
+STAGE_SOURCES = ("fft_warp.cuh", "fft_warp_tma.cuh", "fft_tile.cuh", "stage_io.cuh", "arith.cuh", "arith_pair.cuh",
+                 "warp_plan.h", "fft_stage.h", "generic_stage.cuh", "fft_stage.cu", "fft_tile_df.cu", "fft_tma_256.cu",
+                 "fft_tma_512.cu")
 
 
 def stage_source_hash() -> str:

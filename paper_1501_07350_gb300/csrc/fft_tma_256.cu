@@ -1,0 +1,15 @@
+// fft_tma_256.cu -- instantiations of the asynchronous-output stage kernel
+// (fft_warp_tma.cuh) for 256-point lines.
+#include "fft_warp_tma.cuh"
+
+namespace ofg {
+
+cudaError_t launch_warp_tma_256(const StageLaunch& L, cudaStream_t st, bool* handled)
+{
+    if (L.args.G == 8) return launch_warp_tma_n<256, 8>(L, st, handled);
+    if (L.args.G == 4) return launch_warp_tma_n<256, 4>(L, st, handled);
+    *handled = false;
+    return cudaSuccess;
+}
+
+}  // namespace ofg

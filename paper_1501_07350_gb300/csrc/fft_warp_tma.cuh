@@ -1,0 +1,402 @@
+// fft_warp_tma.cuh -- the double-float warp-per-line stage kernel with an
+// asynchronous output path, for 256- and 512-point lines in tiles of 4 or 8.
+//
+// The radix passes are those of fft_warp.cuh (packed double-float policy,
+// per-pass twiddle tables).  What differs is the output: the last radix pass
+// writes its results into a staging area laid out as the output needs them,
+// and one thread hands the whole tile to the tensor memory accelerator (a TMA
+// tensor store, or one bulk copy per line for contiguous output), which
+// drains it while the CTA goes on with the next tile.
+// Transposed output (the fused transposes of steps (4)-(6), Sec. 3.1.1): the
+// tile's G lines are consecutive in the output at every frequency k, so the
+// staging area is [k][G lines] of 16-byte elements in the swizzle of the
+// tensor store (rows of 128 bytes, 16-byte chunk index XOR row mod 8, for
+// G = 8; rows of 64 bytes, chunk XOR (row / 2) mod 4, for G = 4), which also
+// keeps the last pass's shared-memory writes free of bank conflicts.  The
+// tensor map views the output as (grouped line coordinate, frequency, other
+// line coordinate) with element strides (1, Sk, So).
+//
+// Two tile layouts:
+//   * 256-point lines (DB): two input buffers and a separate staging area;
+//     the next tile's lines are copied (cp.async) while the current tile is
+//     transformed, and the staging area is reused one tile later, after the
+//     copy engine has read it.
+//   * 512-point lines (aliased): one input buffer, which the staging area
+//     overlays once every line's last-pass inputs are in registers; the next
+//     tile's copies start when the copy engine has read the staging area.
+//     Shared memory per CTA is that of the synchronous kernel, so as many
+//     CTAs stay resident; their loads and computations overlap.
+#pragma once
+#include <cuda.h>
+
+#include <cstring>
+
+#include "fft_warp.cuh"
+
+namespace ofg {
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, uint32_t src, int x, int y, int z)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];"
+                 :: "l"(map), "r"(src), "r"(x), "r"(y), "r"(z) : "memory");
+}
+__device__ __forceinline__ void bulk_store(void* dst, uint32_t src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" :: "l"(dst), "r"(src), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the copy engine has read every committed group's shared memory
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// every committed group is complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// make this thread's generic-proxy shared-memory writes visible to the copy engine
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// one warp per line: the passes of a line synchronise its warp only
+template <int WPL>
+__device__ __forceinline__ void line_sync(int) { __syncwarp(); }
+
+// byte offset of output element (frequency k, tile line g) in the transposed
+// staging area: the tensor store's swizzle for rows of G x 16 bytes
+template <int G>
+__device__ __forceinline__ uint32_t staged_offset(int k, int g)
+{
+    if constexpr (G == 8) return (uint32_t)k * 128u + ((uint32_t)(g ^ (k & 7)) << 4);
+    else return (uint32_t)k * 64u + ((uint32_t)(g ^ ((k >> 1) & 3)) << 4);
+}
+
+template <int N, int WPL>
+struct TmaLine {
+    using A = ArDP;
+    using C = ArDP::C;
+    using W = ArDP::W;
+    static constexpr int kPasses = wplan_len(N);
+    static constexpr int LS = warp_line_stride<16>(N);
+
+    // butterflies of pass P taken by part w of the line's threads
+    template <int P>
+    __device__ __forceinline__ static void butterflies(const C* line, const W* __restrict__ tw, int lane, int w,
+                                                       C (*v)[8], bool* ok)
+    {
+        constexpr int R = wplan_radix(N, P);
+        constexpr int m = wplan_m(N, P);
+        constexpr int s = N / (m * R);
+        constexpr int NBF = N / R;
+        constexpr int NB = (NBF + 32 * WPL - 1) / (32 * WPL);
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int b = lane + 32 * (w + WPL * u);
+            ok[u] = NBF % (32 * WPL) == 0 || b < NBF;
+            if (ok[u]) {
+#pragma unroll
+                for (int j = 0; j < R; ++j) v[u][j] = line[wpad<16>(b + j * NBF)];
+                if (m > 1) {
+                    const int k = b % m;
+#pragma unroll
+                    for (int j = 1; j < R; ++j)
+                        v[u][j] = A::mul(v[u][j], A::template warp_twiddle<N>(tw, wtw_offset(N, P), m, j, k, k * s));
+                }
+                Dft<A, R>::run(v[u]);
+            }
+        }
+    }
+
+    // an in-place pass (all but the last)
+    template <int P>
+    __device__ __forceinline__ static void pass(C* line, const W* __restrict__ tw, int lane, int w, int g)
+    {
+        constexpr int R = wplan_radix(N, P);
+        constexpr int m = wplan_m(N, P);
+        constexpr int NBF = N / R;
+        constexpr int NB = (NBF + 32 * WPL - 1) / (32 * WPL);
+        C v[NB][8];
+        bool ok[NB];
+        butterflies<P>(line, tw, lane, w, v, ok);
+        line_sync<WPL>(g);
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            if (ok[u]) {
+                const int b = lane + 32 * (w + WPL * u);
+                const int base = (b / m) * m * R + b % m;
+#pragma unroll
+                for (int q = 0; q < R; ++q) line[wpad<16>(base + m * q)] = v[u][q];
+            }
+        }
+        line_sync<WPL>(g);
+    }
+
+    template <int P>
+    __device__ __forceinline__ static void passes(C* line, const W* __restrict__ tw, int lane, int w, int g)
+    {
+        if constexpr (P < kPasses - 1) {
+            pass<P>(line, tw, lane, w, g);
+            passes<P + 1>(line, tw, lane, w, g);
+        }
+    }
+
+    // 16 output bytes of a result: the stage's output format, conjugated and
+    // scaled on the backward transform's last stage
+    template <bool CONJ_SCALE, bool EXT>
+    __device__ __forceinline__ static uint4 out16(C v, double scale)
+    {
+        if constexpr (CONJ_SCALE) v = A::scale(A::conj(v), scale);
+        if constexpr (EXT) {
+            const double2 d = df_to_double2(A::to_float4(v));
+            uint4 r;
+            r.x = (uint32_t)__double_as_longlong(d.x);
+            r.y = (uint32_t)((unsigned long long)__double_as_longlong(d.x) >> 32);
+            r.z = (uint32_t)__double_as_longlong(d.y);
+            r.w = (uint32_t)((unsigned long long)__double_as_longlong(d.y) >> 32);
+            return r;
+        } else {
+            return make_uint4((uint32_t)v.x, (uint32_t)(v.x >> 32), (uint32_t)v.y, (uint32_t)(v.y >> 32));
+        }
+    }
+
+    // the last pass, into the staging area: [k][G lines] swizzled rows
+    // (transposed output) or [line][k] (contiguous output).  ALIASED: the
+    // staging area overlays the input buffer, so every line's inputs are read
+    // (CTA barrier) before any result is written.
+    template <int G, bool ALIASED, bool CONTIG, bool CONJ_SCALE, bool EXT>
+    __device__ __forceinline__ static void last_pass(const C* line, const W* __restrict__ tw, unsigned char* stage,
+                                                     int lane, int w, int g, double scale)
+    {
+        constexpr int P = kPasses - 1;
+        constexpr int R = wplan_radix(N, P);
+        constexpr int m = wplan_m(N, P);
+        constexpr int NBF = N / R;
+        constexpr int NB = (NBF + 32 * WPL - 1) / (32 * WPL);
+        C v[NB][8];
+        bool ok[NB];
+        butterflies<P>(line, tw, lane, w, v, ok);
+        if constexpr (ALIASED) __syncthreads();
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            if (ok[u]) {
+                const int b = lane + 32 * (w + WPL * u);
+                const int base = (b / m) * m * R + b % m;
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const int k = base + m * q;
+                    const uint32_t off = CONTIG ? (uint32_t)(g * N + k) * 16u : staged_offset<G>(k, g);
+                    *reinterpret_cast<uint4*>(stage + off) = out16<CONJ_SCALE, EXT>(v[u][q], scale);
+                }
+            }
+        }
+    }
+};
+
+// copies of this thread's share of line g (parts w of WPL)
+template <int N, int WPL>
+__device__ __forceinline__ void tma_issue_load(const StageArgs& p, const TileGeom& tg, int g, ArDP::C* line,
+                                               int lane, int w)
+{
+    if (g < tg.valid) {
+        const char* src = reinterpret_cast<const char*>(p.in) + (tg.line0 + g * tg.lstride) * (int64_t)(N * 16);
+#pragma unroll
+        for (int u = 0; u < N / (32 * WPL); ++u) {
+            const int pos = lane + 32 * (w + WPL * u);
+            cp_async<16>(line + wpad<16>(pos), src + pos * 16);
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < N / (32 * WPL); ++u) line[wpad<16>(lane + 32 * (w + WPL * u))] = ArDP::zero();
+    }
+    cp_async_commit();
+}
+
+template <int N, int WPL, bool CONVERT, bool CONJ>
+__device__ __forceinline__ void tma_fix(ArDP::C* line, int lane, int w)
+{
+#pragma unroll
+    for (int u = 0; u < N / (32 * WPL); ++u) {
+        ArDP::C* x = line + wpad<16>(lane + 32 * (w + WPL * u));
+        ArDP::C v;
+        if constexpr (CONVERT) v = Io<ArDP>::from_c128(*reinterpret_cast<const double2*>(x));
+        else v = *x;
+        if constexpr (CONJ) v = ArDP::conj(v);
+        *x = v;
+    }
+}
+
+// whether a line length runs with one input buffer and the staging area on it
+template <int N>
+constexpr bool tma_aliased() { return N >= 512; }
+
+template <int N, int G>
+constexpr size_t tma_stage_bytes() { return (size_t)N * G * 16; }
+template <int N, int G>
+constexpr size_t tma_smem_bytes()
+{
+    // 1024-byte alignment slack, then the staging area and two input buffers,
+    // or the one input buffer the staging area overlays
+    return tma_aliased<N>() ? 1024 + (size_t)G * warp_line_stride<16>(N) * 16
+                            : 1024 + tma_stage_bytes<N, G>() + 2 * (size_t)G * warp_line_stride<16>(N) * 16;
+}
+
+template <int N, int G, bool CONTIG, bool CONJ_SCALE, bool EXT>
+__global__ void __launch_bounds__(32 * G, G == 8 ? 2 : 4)
+fft_warp_tma_kernel(const StageArgs p, int64_t ntiles, const __grid_constant__ CUtensorMap tmap)
+{
+    constexpr int WPL = 1;
+    constexpr bool ALIASED = tma_aliased<N>();
+    using L = TmaLine<N, WPL>;
+    using C = ArDP::C;
+    constexpr int LS = L::LS;
+    static_assert(tma_stage_bytes<N, G>() <= (size_t)G * LS * 16 || !ALIASED, "staging must fit the buffer");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t base = smem_addr(smem_raw);
+    unsigned char* aligned = smem_raw + (((base + 1023u) & ~1023u) - base);
+    unsigned char* stage = aligned;
+    C* cur = reinterpret_cast<C*>(ALIASED ? aligned : aligned + tma_stage_bytes<N, G>());
+    C* nxt = ALIASED ? cur : cur + G * LS;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = warp, w = 0;
+    const ArDP::W* tw = ArDP::table(p.tw, N);
+    const bool convert = p.in_fmt == FMT_C128;
+
+    int64_t tile = blockIdx.x;
+    if (!ALIASED && tile < ntiles) tma_issue_load<N, WPL>(p, tile_geom(p, tile, G), g, cur + g * LS, lane, w);
+    for (; tile < ntiles; tile += gridDim.x) {
+        const TileGeom tg = tile_geom(p, tile, G);
+        C* line = cur + g * LS;
+        if (ALIASED) {
+            // the previous tile's store has read the buffer: copy this tile in
+            if (tid == 0) bulk_wait_read_all();
+            __syncthreads();
+            tma_issue_load<N, WPL>(p, tg, g, line, lane, w);
+        }
+        cp_async_wait_all();
+        if (convert) { if (p.conj_in) tma_fix<N, WPL, true, true>(line, lane, w); else tma_fix<N, WPL, true, false>(line, lane, w); }
+        else if (p.conj_in) tma_fix<N, WPL, false, true>(line, lane, w);
+        line_sync<WPL>(g);
+        if (!ALIASED) {
+            const int64_t next = tile + gridDim.x;
+            if (next < ntiles) tma_issue_load<N, WPL>(p, tile_geom(p, next, G), g, nxt + g * LS, lane, w);
+        }
+        L::template passes<0>(line, tw, lane, w, g);
+        if (!ALIASED) {
+            if (tid == 0) bulk_wait_read_all();      // the previous tile's store has read the staging area
+            __syncthreads();
+        }
+        L::template last_pass<G, ALIASED, CONTIG, CONJ_SCALE, EXT>(line, tw, stage, lane, w, g, p.scale);
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            if constexpr (!CONTIG) {
+#pragma unroll
+                for (int kb = 0; kb < (N + 255) / 256; ++kb)
+                    tma_store_3d(&tmap, smem_addr(stage) + (uint32_t)kb * 256u * (uint32_t)(G * 16),
+                                 (int)((tile % p.ngroups) * G * 4), kb * 256, (int)(tile / p.ngroups));
+            } else {
+                char* first = reinterpret_cast<char*>(p.out) + tg.obase * 16;
+                for (int gg = 0; gg < tg.valid; ++gg)
+                    bulk_store(first + (int64_t)gg * tg.ostride * 16, smem_addr(stage) + (uint32_t)gg * N * 16u, N * 16u);
+            }
+            bulk_commit();
+        }
+        C* t = cur; cur = nxt; nxt = t;
+    }
+    cp_async_wait_all();
+    if (tid == 0) bulk_wait_all();
+}
+
+// host side ----------------------------------------------------------------
+
+using TensorMapEncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                       const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                       CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+inline TensorMapEncodeFn tensor_map_encoder()
+{
+    static TensorMapEncodeFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<TensorMapEncodeFn>(f);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// The transposed output as a 3-D tensor of 4-byte words: (grouped line
+// coordinate x 4, frequency, other line coordinate); box (8 lines, 256 or n
+// frequencies, 1).  false if the stage's geometry has no such view.
+inline bool transposed_store_map(const StageArgs& a, int G, CUtensorMap* map)
+{
+    const int64_t Mg = a.group_i2 ? a.M2 : a.M1, Mo = a.group_i2 ? a.M1 : a.M2;
+    const int64_t Sg = a.group_i2 ? a.S2 : a.S1, So = a.group_i2 ? a.S1 : a.S2;
+    if (Sg != 1 || a.Sk < 1 || Mg * 4 > (int64_t)0xFFFFFFFF || Mo > 0xFFFFFFFF) return false;
+    if ((reinterpret_cast<uintptr_t>(a.out) & 15) != 0) return false;
+    TensorMapEncodeFn enc = tensor_map_encoder();
+    if (!enc) return false;
+    const int64_t s1 = a.Sk * 16;
+    const int64_t s2 = Mo > 1 ? So * 16 : s1 * a.n;
+    if (s1 >= ((int64_t)1 << 40) || s2 >= ((int64_t)1 << 40) || s2 <= 0) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)(Mg * 4), (cuuint64_t)a.n, (cuuint64_t)Mo};
+    const cuuint64_t strides[2] = {(cuuint64_t)s1, (cuuint64_t)s2};
+    const cuuint32_t box[3] = {(cuuint32_t)(4 * G), (cuuint32_t)(a.n < 256 ? a.n : 256), 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, a.out, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               G == 8 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+template <int N, int G, bool CONTIG, bool CONJ_SCALE, bool EXT>
+cudaError_t launch_warp_tma_v(const StageLaunch& L, const CUtensorMap& map, cudaStream_t st)
+{
+    auto kern = fft_warp_tma_kernel<N, G, CONTIG, CONJ_SCALE, EXT>;
+    const size_t smem = tma_smem_bytes<N, G>();
+    static int cached[kMaxDevices] = {};
+    int* slot = device_slot(cached);
+    int per_sm = slot ? *slot : 0;
+    if (per_sm == 0) {
+        cudaError_t e = persistent_ctas_per_sm((const void*)kern, 32 * G, smem, &per_sm);
+        if (e) return e;
+        if (slot) *slot = per_sm;
+    }
+    const int64_t ntiles = L.grid;
+    int64_t grid = (int64_t)L.sms * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, 32 * G, smem, st>>>(L.args, ntiles, map);
+    return cudaGetLastError();
+}
+
+// The asynchronous-output kernel for n = 256 / 512 and 4 or 8 lines per CTA,
+// when the stage's output has the view it needs; *handled = false otherwise.
+template <int N, int G>
+cudaError_t launch_warp_tma_n(const StageLaunch& L, cudaStream_t st, bool* handled)
+{
+    const StageArgs& a = L.args;
+    CUtensorMap map;
+    std::memset(&map, 0, sizeof(map));
+    const bool contig = a.contig_store != 0;
+    if (contig) {
+        if (a.group_i2 || a.S1 != a.n || a.Sk != 1 || (reinterpret_cast<uintptr_t>(a.out) & 15) != 0) {
+            *handled = false;
+            return cudaSuccess;
+        }
+    } else if (!transposed_store_map(a, G, &map)) {
+        *handled = false;
+        return cudaSuccess;
+    }
+    *handled = true;
+    const bool ext = a.out_fmt != FMT_DF, cs = a.conj_out != 0;
+    if (contig) {
+        if (cs) return ext ? launch_warp_tma_v<N, G, true, true, true>(L, map, st) : launch_warp_tma_v<N, G, true, true, false>(L, map, st);
+        return ext ? launch_warp_tma_v<N, G, true, false, true>(L, map, st) : launch_warp_tma_v<N, G, true, false, false>(L, map, st);
+    }
+    if (cs) return ext ? launch_warp_tma_v<N, G, false, true, true>(L, map, st) : launch_warp_tma_v<N, G, false, true, false>(L, map, st);
+    return ext ? launch_warp_tma_v<N, G, false, false, true>(L, map, st) : launch_warp_tma_v<N, G, false, false, false>(L, map, st);
+}
+
+}  // namespace ofg
