@@ -65,6 +65,12 @@ def _configure(lib):
     lib.oracle_fft3d.argtypes = [i64] * 4 + [i32, vp, vp, vp, vp]
     lib.oracle_rfft3d.restype = i32
     lib.oracle_rfft3d.argtypes = [i64] * 4 + [i32, vp, vp, vp, vp]
+    lib.oracle_nd_boundaries.restype = i32
+    lib.oracle_nd_boundaries.argtypes = [i32, p64, i32, i64, p64]
+    lib.oracle_nd_redistribute.restype = i32
+    lib.oracle_nd_redistribute.argtypes = [i32, p64, i64, i32, i32, vp, vp, vp]
+    lib.oracle_fftnd.restype = i32
+    lib.oracle_fftnd.argtypes = [i32, p64, i64, i32, vp, vp]
     return lib
 
 
@@ -231,3 +237,49 @@ def rel_l2(y, y_ref) -> float:
     num = np.sum(np.longdouble(d.real) ** 2 + np.longdouble(d.imag) ** 2)
     den = np.sum(np.longdouble(y_ref.real) ** 2 + np.longdouble(y_ref.imag) ** 2)
     return float(np.sqrt(num / den))
+
+
+# ------------------------------------------------------ D-dimensional --
+
+def _dims64(dims):
+    return (ctypes.c_int64 * len(dims))(*[int(v) for v in dims])
+
+
+def nd_boundaries(dims, Np: int, s: int) -> np.ndarray:
+    """Eqs. 2-4 of ordering s (1..D) of a D-dimensional array: xs[0..Np].
+
+    Ordering s is (d_D, ..., d_{D-s+2}, d_1, ..., d_{D-s+1}) (slowest first),
+    decomposed with (N1, N2, N3) = (first dim, second dim, product of the rest)."""
+    xs = np.zeros(Np + 1, dtype=np.int64)
+    rc = _load().oracle_nd_boundaries(len(dims), _dims64(dims), s, Np,
+                                      xs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    if rc != 0:
+        raise ValueError("decomposition undefined")
+    return xs
+
+
+def nd_redistribute(dims, Np: int, s: int, forward: bool, src):
+    """Steps (4)-(6) from ordering s to s+1 (forward) or s+1 to s: (dst, counts)."""
+    src = _c128(src).reshape(-1)
+    dst = np.full_like(src, np.nan + 1j * np.nan)
+    C = np.zeros((Np, Np), dtype=np.int64)
+    rc = _load().oracle_nd_redistribute(len(dims), _dims64(dims), Np, s, 1 if forward else 0,
+                                        _ptr(src), _ptr(dst), _ptr(C))
+    if rc != 0:
+        raise ValueError("redistribution undefined or inconsistent")
+    return dst, C
+
+
+def fftnd(A, dims, Np: int, direction: int = FORWARD) -> np.ndarray:
+    """D-dimensional C2C transform under the decomposition over Np ranks (D = 3..8).
+
+    forward: A is the array as given (ordering 1), the result is in ordering D
+    (the axes reversed, d_D slowest); backward: the reverse, divided by N."""
+    A = _c128(A).reshape(-1)
+    if A.size != int(np.prod(dims)):
+        raise ValueError("size mismatch")
+    out = np.empty_like(A)
+    rc = _load().oracle_fftnd(len(dims), _dims64(dims), Np, direction, _ptr(A), _ptr(out))
+    if rc != 0:
+        raise ValueError("decomposition undefined for these dims and Np")
+    return out

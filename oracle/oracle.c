@@ -571,3 +571,204 @@ int oracle_fft3d(int64_t Na, int64_t Nb, int64_t Nc, int64_t Np, int dir,
     free(t0); free(t1);
     return rc ? -1 : 0;
 }
+
+/* ============================================= D-dimensional transforms == */
+
+/* The paper cites 4-D and 5-D transforms under the same decomposition (Sec. 1)
+ * without giving their transpose orders.  Reading taken (generalising the
+ * 3-D order abc -> cab -> cba of Sec. 2): for A[N_1]...[N_D] (axis d_D
+ * fastest), ordering s = 1..D is
+ *     (d_D, d_{D-1}, ..., d_{D-s+2}, d_1, d_2, ..., d_{D-s+1}),
+ * i.e. each transpose moves the axis just transformed (the fastest) behind
+ * the axes moved before it.  Stage s transforms the fastest axis of
+ * ordering s; the forward result is left in ordering D (d_D ... d_1, i.e.
+ * the reversed axes); the backward transform runs the orderings in reverse
+ * and divides by N.  Each ordering is decomposed by Eqs. 2-9 with
+ * (N1, N2, N3) = (its first dimension, its second, the product of the
+ * rest): the row-wise 1-D translation of Eq. 1 with the trailing axes
+ * collapsed, so every rank holds whole lines of the fastest axis. */
+
+#define ORACLE_MAX_DIMS 8
+
+/* axes[j] = the original axis (0 = d_1) at position j of ordering s */
+static void nd_axes(int D, int s, int axes[])
+{
+    int k = 0;
+    for (int i = 0; i < s - 1; ++i) axes[k++] = D - 1 - i;
+    for (int i = 0; i < D - s + 1; ++i) axes[k++] = i;
+}
+
+/* Eqs. 2-4 of ordering s: boundaries xs[0..Np] (returns -1 if undefined) */
+static int nd_boundaries(int D, const int64_t* n, int s, int64_t Np, int64_t* xs)
+{
+    int axes[ORACLE_MAX_DIMS];
+    nd_axes(D, s, axes);
+    int64_t rest = 1;
+    for (int j = 2; j < D; ++j) rest *= n[axes[j]];
+    return oracle_boundaries(n[axes[0]], n[axes[1]], rest, Np, xs);
+}
+
+/* Eq. 1 in ordering s: coordinates v (per original axis) -> 1-D index */
+static int64_t nd_index(int D, const int64_t* n, int s, const int64_t* v)
+{
+    int axes[ORACLE_MAX_DIMS];
+    nd_axes(D, s, axes);
+    int64_t x = 0;
+    for (int j = 0; j < D; ++j) x = x * n[axes[j]] + v[axes[j]];
+    return x;
+}
+
+/* the inverse: 1-D index of ordering s -> coordinates */
+static void nd_point(int D, const int64_t* n, int s, int64_t x, int64_t* v)
+{
+    int axes[ORACLE_MAX_DIMS];
+    nd_axes(D, s, axes);
+    for (int j = D - 1; j >= 0; --j) {
+        v[axes[j]] = x % n[axes[j]];
+        x /= n[axes[j]];
+    }
+}
+
+/* Steps (1)-(3) in ordering s: every rank transforms the complete lines of
+ * the fastest axis of its box. */
+static int nd_transform_stage(int D, const int64_t* n, int s, int64_t Np, cplx* data, int sign)
+{
+    int axes[ORACLE_MAX_DIMS];
+    nd_axes(D, s, axes);
+    int64_t* xs = (int64_t*)malloc(sizeof(int64_t) * (size_t)(Np + 1));
+    if (nd_boundaries(D, n, s, Np, xs)) { free(xs); return -1; }
+    int64_t len = n[axes[D - 1]];
+    cplx* W = make_table(len, sign);
+    cplx* buf = (cplx*)malloc(sizeof(cplx) * (size_t)len);
+    cplx* res = (cplx*)malloc(sizeof(cplx) * (size_t)len);
+    for (int64_t r = 0; r < Np; ++r)
+        for (int64_t x = xs[r]; x < xs[r + 1]; x += len) {
+            memcpy(buf, data + x, sizeof(cplx) * (size_t)len);
+            fft_rec(len, buf, 1, res, W, len);
+            memcpy(data + x, res, sizeof(cplx) * (size_t)len);
+        }
+    free(W); free(buf); free(res); free(xs);
+    return 0;
+}
+
+/* Steps (4)-(6) from ordering s_src to ordering s_dst, literally: pack per
+ * destination rank in ascending source index, communicate in order of
+ * source rank, unpack.  C[r*Np+s] receives the counts. */
+static int nd_redistribute(int D, const int64_t* n, int s_src, int s_dst, int64_t Np,
+                           const cplx* src, cplx* dst, int64_t* C)
+{
+    int64_t N = 1;
+    for (int j = 0; j < D; ++j) N *= n[j];
+    int64_t* xs_src = (int64_t*)malloc(sizeof(int64_t) * (size_t)(Np + 1));
+    int64_t* xs_dst = (int64_t*)malloc(sizeof(int64_t) * (size_t)(Np + 1));
+    if (nd_boundaries(D, n, s_src, Np, xs_src) || nd_boundaries(D, n, s_dst, Np, xs_dst)) {
+        free(xs_src); free(xs_dst);
+        return -1;
+    }
+    int64_t* cnt = (int64_t*)calloc((size_t)(Np * Np), sizeof(int64_t));
+    int64_t v[ORACLE_MAX_DIMS];
+    for (int64_t r = 0; r < Np; ++r)
+        for (int64_t x = xs_src[r]; x < xs_src[r + 1]; ++x) {
+            nd_point(D, n, s_src, x, v);
+            cnt[r * Np + owner_of(xs_dst, Np, nd_index(D, n, s_dst, v))] += 1;
+        }
+    int64_t* sdispl = (int64_t*)malloc(sizeof(int64_t) * (size_t)(Np * Np));
+    int64_t* rdispl = (int64_t*)malloc(sizeof(int64_t) * (size_t)(Np * Np));
+    for (int64_t r = 0; r < Np; ++r) {
+        int64_t off = xs_src[r];
+        for (int64_t s = 0; s < Np; ++s) { sdispl[r * Np + s] = off; off += cnt[r * Np + s]; }
+    }
+    for (int64_t s = 0; s < Np; ++s) {
+        int64_t off = xs_dst[s];
+        for (int64_t r = 0; r < Np; ++r) { rdispl[s * Np + r] = off; off += cnt[r * Np + s]; }
+    }
+    /* (4) pack */
+    int64_t* sidx = (int64_t*)malloc(sizeof(int64_t) * (size_t)N);
+    cplx* sval = (cplx*)malloc(sizeof(cplx) * (size_t)N);
+    int64_t* fill = (int64_t*)calloc((size_t)(Np * Np), sizeof(int64_t));
+    for (int64_t r = 0; r < Np; ++r)
+        for (int64_t x = xs_src[r]; x < xs_src[r + 1]; ++x) {
+            nd_point(D, n, s_src, x, v);
+            int64_t y = nd_index(D, n, s_dst, v);
+            int64_t s = owner_of(xs_dst, Np, y);
+            int64_t pos = sdispl[r * Np + s] + fill[r * Np + s]++;
+            sidx[pos] = y;
+            sval[pos] = src[x];
+        }
+    /* (5) communicate */
+    int64_t* ridx = (int64_t*)malloc(sizeof(int64_t) * (size_t)N);
+    cplx* rval = (cplx*)malloc(sizeof(cplx) * (size_t)N);
+    for (int64_t s = 0; s < Np; ++s)
+        for (int64_t r = 0; r < Np; ++r) {
+            int64_t len = cnt[r * Np + s];
+            memcpy(ridx + rdispl[s * Np + r], sidx + sdispl[r * Np + s], sizeof(int64_t) * (size_t)len);
+            memcpy(rval + rdispl[s * Np + r], sval + sdispl[r * Np + s], sizeof(cplx) * (size_t)len);
+        }
+    /* (6) unpack */
+    int bad = 0;
+    for (int64_t s = 0; s < Np; ++s)
+        for (int64_t p = xs_dst[s]; p < xs_dst[s + 1]; ++p) {
+            int64_t y = ridx[p];
+            if (y < xs_dst[s] || y >= xs_dst[s + 1]) { bad = 1; continue; }
+            dst[y] = rval[p];
+        }
+    if (C) memcpy(C, cnt, sizeof(int64_t) * (size_t)(Np * Np));
+    free(xs_src); free(xs_dst); free(cnt); free(sdispl); free(rdispl);
+    free(sidx); free(sval); free(fill); free(ridx); free(rval);
+    return bad ? -1 : 0;
+}
+
+/* Eqs. 2-4 of ordering s (1..D) of a D-dimensional array: xs[0..Np]. */
+int oracle_nd_boundaries(int D, const int64_t* n, int s, int64_t Np, int64_t* xs)
+{
+    if (D < 2 || D > ORACLE_MAX_DIMS || s < 1 || s > D) return -1;
+    return nd_boundaries(D, n, s, Np, xs);
+}
+
+/* One transpose alone: ordering s -> s + 1 (step > 0) or s + 1 -> s. */
+int oracle_nd_redistribute(int D, const int64_t* n, int64_t Np, int s, int forward,
+                           const cplx* src, cplx* dst, int64_t* C)
+{
+    if (D < 3 || D > ORACLE_MAX_DIMS || s < 1 || s >= D) return -1;
+    return forward ? nd_redistribute(D, n, s, s + 1, Np, src, dst, C)
+                   : nd_redistribute(D, n, s + 1, s, Np, src, dst, C);
+}
+
+/* The whole D-dimensional transform under the decomposition over Np ranks.
+ * dir = -1: A in ordering 1 (the array as given), result in ordering D;
+ * dir = +1: A in ordering D, result in ordering 1, divided by N. */
+int oracle_fftnd(int D, const int64_t* n, int64_t Np, int dir, const cplx* in, cplx* out)
+{
+    if (D < 3 || D > ORACLE_MAX_DIMS || (dir != -1 && dir != 1)) return -1;
+    int64_t N = 1;
+    for (int j = 0; j < D; ++j) N *= n[j];
+    cplx* t0 = (cplx*)malloc(sizeof(cplx) * (size_t)N);
+    cplx* t1 = (cplx*)malloc(sizeof(cplx) * (size_t)N);
+    memcpy(t0, in, sizeof(cplx) * (size_t)N);
+    int rc = 0;
+    if (dir == -1) {
+        for (int s = 1; s <= D; ++s) {
+            rc |= nd_transform_stage(D, n, s, Np, t0, -1);
+            if (s < D) {
+                rc |= nd_redistribute(D, n, s, s + 1, Np, t0, t1, NULL);
+                cplx* t = t0; t0 = t1; t1 = t;
+            }
+        }
+        memcpy(out, t0, sizeof(cplx) * (size_t)N);
+    } else {
+        for (int s = D; s >= 1; --s) {
+            rc |= nd_transform_stage(D, n, s, Np, t0, 1);
+            if (s > 1) {
+                rc |= nd_redistribute(D, n, s, s - 1, Np, t0, t1, NULL);
+                cplx* t = t0; t0 = t1; t1 = t;
+            }
+        }
+        const double count = (double)N;
+        for (int64_t i = 0; i < N; ++i) {
+            out[i].re = t0[i].re / count;
+            out[i].im = t0[i].im / count;
+        }
+    }
+    free(t0); free(t1);
+    return rc ? -1 : 0;
+}

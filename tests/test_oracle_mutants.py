@@ -47,6 +47,12 @@ MUTANTS = {
                                         "for (int64_t i = 0; i < Nc; ++i) x[xx + i] = res[i].im;"),
     "real stage keeps one frequency too few": ("memcpy(half + l * Nch, res, sizeof(cplx) * (size_t)Nch);",
                                                "memcpy(half + l * Nch, res, sizeof(cplx) * (size_t)(Nch - 1));"),
+    "D-dimensional ordering keeps the moved axes in forward order": (
+        "for (int i = 0; i < s - 1; ++i) axes[k++] = D - 1 - i;",
+        "for (int i = 0; i < s - 1; ++i) axes[k++] = D - s + 1 + i;"),
+    "D-dimensional decomposition drops the trailing product": (
+        "for (int j = 2; j < D; ++j) rest *= n[axes[j]];",
+        "for (int j = 2; j < 3; ++j) rest *= n[axes[j]];"),
 }
 
 
@@ -126,6 +132,18 @@ def _checks():
         ref = np.fft.irfftn(np.transpose(H.reshape(Nch, Nb, Na), (2, 1, 0)), s=(Na, Nb, Nc), axes=(0, 1, 2))
         ok &= _close(xb, ref.reshape(-1))
     out["real transforms vs numpy"] = bool(ok)
+    # D-dimensional transforms vs numpy fftn (result in the reversed axes)
+    ok = True
+    for dims, P in [((4, 3, 5, 2), 8), ((2, 3, 2, 2, 3), 6), ((3, 4, 2, 2, 5), 2)]:
+        x = synth.complex_field(dims, seed=sum(dims) + P)
+        rev = tuple(range(len(dims) - 1, -1, -1))
+        try:
+            y = oracle.fftnd(x, dims, P, oracle.FORWARD)
+        except ValueError:
+            ok = False
+            continue
+        ok &= _close(y, np.transpose(np.fft.fftn(x), rev))
+    out["D-dimensional transforms vs numpy"] = bool(ok)
     return out
 
 
