@@ -739,6 +739,21 @@ def measure_learned(of, torch, stream, Ps=(64, 256, 1024), reps=5):
     out["mean_regret"] = round(sum(regrets) / len(regrets), 4)
     out["max_regret"] = round(max(regrets), 4)
     out["target"] = "within 5% of exhaustive autotuning"
+    # the committed dataset: regret on the held-out benchmark problems, and on
+    # whole shape families held out of training (models trained on the GPU here)
+    rows = learned.load_rows()
+    tr, te = learned.split(rows)
+    ps, _ = learned.train(tr)
+    ev = learned.evaluate(te, ps)
+    out["dataset_held_out"] = {"summary": learned.summary(ev),
+                               "per_problem": [{"shape": e["shape"], "P": e["P"], "dtype": e["dtype"],
+                                                "regret": round(e["regret"], 4),
+                                                "speedup_vs_default": round(e["speedup_vs_default"], 4)}
+                                               for e in ev]}
+    out["family_held_out"] = {k: {"train_problems": v["train_problems"], "summary": v["summary"],
+                                  "per_problem": [{"shape": e["shape"], "P": e["P"], "dtype": e["dtype"],
+                                                   "regret": round(e["regret"], 4)} for e in v["problems"]]}
+                              for k, v in learned.evaluate_families(rows).items()}
     del x, y
     torch.cuda.empty_cache()
     return out

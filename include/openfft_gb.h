@@ -380,6 +380,14 @@ int openfft_batch_debug(openfft_plan_t plan, int what, long long value);
  * (value = 0 undoes it).  Nothing is in flight when a wait runs out. */
 int openfft_tc_debug(int what, long long value);
 
+/* Test control: the nth device allocation the library makes from now on
+ * (plans, batched and distributed plans, host-buffer staging, tuning
+ * buffers) fails as if the device were out of memory; the call making it
+ * returns OPENFFT_ERR_NOMEM after freeing what it had allocated.  nth = 0
+ * switches it off; it switches itself off after the failure.  INVALID_ARG
+ * for nth < 0.  Not thread-safe with concurrent plan creation. */
+int openfft_debug_alloc_fail(long long nth);
+
 /* ------------------------------------------- over several devices ----- */
 
 /* The transform over G devices (one process each), device g holding the
@@ -444,6 +452,40 @@ int openfft_dist_stage(openfft_dist_plan_t plan, int stage, int dir, const void*
  * openfft_dist_elem_bytes elements, asynchronous on the plan's stream. */
 int openfft_dist_pack(openfft_dist_plan_t plan, int exchange, const void* src, void* send);
 int openfft_dist_unpack(openfft_dist_plan_t plan, int exchange, const void* recv, void* dst);
+
+/* -------------------------------------------- 4-D and 5-D transforms ---- */
+
+/* D-dimensional transforms (D = 3, 4, 5) under the same decomposition.  The
+ * paper cites 4-D and 5-D transforms (Sec. 1) without their transpose
+ * orders; this library's reading generalises Sec. 2's abc -> cab -> cba:
+ * ordering s = 1..D of A[N_1]...[N_D] (d_D fastest) is
+ * (d_D, ..., d_{D-s+2}, d_1, ..., d_{D-s+1}); stage s transforms the
+ * fastest axis of ordering s with the transpose to ordering s + 1 fused into
+ * its store.  FORWARD takes the array as given (ordering 1) and leaves the
+ * spectrum in ordering D, the reversed axes: X[k_1..k_D] at index
+ * ((k_D N_{D-1} + k_{D-1}) N_{D-2} + ...) N_1 + k_1.  BACKWARD takes
+ * ordering D, returns ordering 1 and divides by N.  Each ordering is
+ * decomposed by Eqs. 2-9 with (N1, N2, N3) = (its first dimension, its
+ * second, the product of the rest), so P <= min over orderings of N1 N2
+ * (OPENFFT_ERR_P_TOO_LARGE otherwise).  dims: host array of ndim axis
+ * lengths, each with factors 2, 3, 5, 7 only and <= 2048.  Arithmetic as for
+ * openfft_plan's default candidate (double-float for OPENFFT_C2C_F64, FP32
+ * for OPENFFT_C2C_F32); the plan owns an N-element workspace and the twiddle
+ * tables; `in` / `out` are caller-owned device arrays of N elements, in !=
+ * out.  Asynchronous on the plan's stream. */
+typedef struct openfft_nd_plan_s* openfft_nd_plan_t;
+openfft_nd_plan_t openfft_nd_plan(int ndim, const int* dims, int P, int dtype);   /* NULL on error */
+int openfft_nd_exec(openfft_nd_plan_t plan, const void* in, void* out, int dir);
+void openfft_nd_destroy(openfft_nd_plan_t plan);                                  /* NULL-safe */
+int openfft_nd_set_stream(openfft_nd_plan_t plan, void* stream);                  /* cudaStream_t */
+/* Box of `rank` in the input (which = 0: ordering 1) or output (which = 1:
+ * ordering D) decomposition: 1-D offset x^s and element count (Eqs. 3-4). */
+int openfft_nd_box(openfft_nd_plan_t plan, int which, int rank, int64_t* offset, int64_t* count);
+/* Host only: the same box for any ordering s = 1..ndim, and the P x P count
+ * matrix (row = sender) of transpose `exchange`: s -> s + 1 for exchange = s
+ * > 0, s + 1 -> s for exchange = -s (an O(N) enumeration). */
+int openfft_nd_decomp_box(int ndim, const int* dims, int P, int ordering, int rank, int64_t* offset, int64_t* count);
+int openfft_nd_decomp_counts(int ndim, const int* dims, int P, int exchange, int64_t* PxP);
 
 /* ------------------------------------------------- allocation-free ----- */
 

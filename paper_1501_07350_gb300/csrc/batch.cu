@@ -281,7 +281,7 @@ int batch_create(int count, const int* dims, const int* P, int dtype, int sms, B
     auto twiddle_for = [&](int n) -> const void* {
         for (size_t k = 0; k < tw_len.size(); ++k) if (tw_len[k] == n) return b->twiddles[k];
         void* t = nullptr;
-        if (cudaMalloc(&t, twiddle_bytes(n, twf))) return nullptr;
+        if (dev_malloc((void**)&t, twiddle_bytes(n, twf))) return nullptr;
         if (launch_twiddles(n, twf, t, nullptr)) { cudaFree(t); return nullptr; }
         tw_len.push_back(n);
         b->twiddles.push_back(t);
@@ -294,7 +294,7 @@ int batch_create(int count, const int* dims, const int* P, int dtype, int sms, B
         const int64_t N = Na * Nb * Nc;
         b->N.push_back(N);
         void* sc = nullptr;
-        if (cudaMalloc(&sc, (size_t)N * E)) { cudaGetLastError(); free_batch(b); return fail(OPENFFT_ERR_NOMEM, "batched workspace"); }
+        if (dev_malloc((void**)&sc, (size_t)N * E)) { cudaGetLastError(); free_batch(b); return fail(OPENFFT_ERR_NOMEM, "batched workspace"); }
         b->scratch.push_back(sc);
         // forward / backward stage geometry, as in the fused single-transform path
         struct Geo { int64_t n, M1, M2, S1, S2, Sk; int g2, contig, in_fmt, out_fmt, cin, cout; double scale; };
@@ -332,12 +332,12 @@ int batch_create(int count, const int* dims, const int* P, int dtype, int sms, B
             }
     }
     b->ctr_bytes = sizeof(BatchCounters) + sizeof(unsigned) * (size_t)3 * count;
-    if (cudaMalloc(&b->d_stages, st.size() * sizeof(StageArgs)) ||
-        cudaMalloc(&b->d_item_base, sizeof(int64_t) * (size_t)(2 * (3 * count + 1))) ||
-        cudaMalloc(&b->d_need, sizeof(unsigned) * (size_t)(2 * 3 * count)) ||
-        cudaMalloc(&b->d_ptrs, sizeof(void*) * (size_t)(2 * count)) ||
-        cudaMalloc(&b->d_scratch, sizeof(void*) * (size_t)count) ||
-        cudaMalloc(&b->d_ctr, b->ctr_bytes) ||
+    if (dev_malloc((void**)&b->d_stages, st.size() * sizeof(StageArgs)) ||
+        dev_malloc((void**)&b->d_item_base, sizeof(int64_t) * (size_t)(2 * (3 * count + 1))) ||
+        dev_malloc((void**)&b->d_need, sizeof(unsigned) * (size_t)(2 * 3 * count)) ||
+        dev_malloc((void**)&b->d_ptrs, sizeof(void*) * (size_t)(2 * count)) ||
+        dev_malloc((void**)&b->d_scratch, sizeof(void*) * (size_t)count) ||
+        dev_malloc((void**)&b->d_ctr, b->ctr_bytes) ||
         cudaMallocHost(&b->h_ptrs, sizeof(void*) * (size_t)(2 * count))) {
         cudaGetLastError();
         free_batch(b);

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -24,6 +25,25 @@
 #include "batch.h"
 
 using namespace ofg;
+
+namespace ofg {
+
+// 0: allocations behave; k > 0: the k-th allocation from now fails (once)
+static std::atomic<long long> g_alloc_fail_at{0};
+
+cudaError_t dev_malloc(void** ptr, size_t bytes)
+{
+    long long k = g_alloc_fail_at.load();
+    while (k > 0 && !g_alloc_fail_at.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k == 1) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(ptr, bytes);
+}
+
+}  // namespace ofg
 
 namespace {
 
@@ -577,7 +597,7 @@ int time_candidates(openfft_plan_s* p, std::vector<float>& ms)
 {
     const size_t bytes = (size_t)p->N * p->elem_bytes;
     void *tin = nullptr, *tout = nullptr;
-    if (cudaMalloc(&tin, bytes) || cudaMalloc(&tout, bytes)) {
+    if (dev_malloc((void**)&tin, bytes) || dev_malloc((void**)&tout, bytes)) {
         cudaGetLastError(); cudaFree(tin);
         return fail(OPENFFT_ERR_NOMEM, "tuning buffers");
     }
@@ -615,6 +635,13 @@ extern "C" {
 
 const char* openfft_last_error(void) { return g_err.c_str(); }
 int openfft_last_status(void) { return g_status; }
+
+int openfft_debug_alloc_fail(long long nth)
+{
+    if (nth < 0) return fail(OPENFFT_ERR_INVALID_ARG, "nth must be >= 0");
+    g_alloc_fail_at.store(nth);
+    return OPENFFT_OK;
+}
 
 int openfft_decomp_degree(int Na, int Nb, int Nc, int P, int layout)
 {
@@ -675,7 +702,7 @@ openfft_plan_t openfft_plan(int Na, int Nb, int Nc, int P, int dtype)
     if ((e = stage_kernels_init(200 * 1024))) { cuda_fail(e, "kernel attributes"); delete p; return nullptr; }
     p->elem_bytes = c64 ? 8 : 16;
     const size_t bytes = (size_t)p->N * p->elem_bytes;
-    if (cudaMalloc(&p->bufA, bytes) || cudaMalloc(&p->bufB, bytes)) {
+    if (dev_malloc((void**)&p->bufA, bytes) || dev_malloc((void**)&p->bufB, bytes)) {
         cudaGetLastError();
         fail(OPENFFT_ERR_NOMEM, "workspace allocation failed");
         free_plan(p);
@@ -686,7 +713,7 @@ openfft_plan_t openfft_plan(int Na, int Nb, int Nc, int P, int dtype)
         const int fmts[2] = {c64 ? FMT_C64 : FMT_C128, c64 ? -1 : FMT_DF};
         for (int f : fmts) {
             if (f < 0) continue;
-            if (cudaMalloc(&p->tw[ax][f], twiddle_bytes(lens[ax], f))) {
+            if (dev_malloc((void**)&p->tw[ax][f], twiddle_bytes(lens[ax], f))) {
                 cudaGetLastError();
                 fail(OPENFFT_ERR_NOMEM, "twiddle allocation failed");
                 free_plan(p);
@@ -702,7 +729,7 @@ openfft_plan_t openfft_plan(int Na, int Nb, int Nc, int P, int dtype)
         for (int ax = 0; ax < 3; ++ax) {
             int R = 0, S = 0;
             if (!dftgemm_factor(lens[ax], tf32, &R, &S)) continue;
-            if (cudaMalloc(&p->bimg[ax], dftgemm_image_bytes(lens[ax], R, S, tf32))) {
+            if (dev_malloc((void**)&p->bimg[ax], dftgemm_image_bytes(lens[ax], R, S, tf32))) {
                 cudaGetLastError();
                 fail(OPENFFT_ERR_NOMEM, "operand image allocation failed");
                 free_plan(p);
@@ -722,9 +749,9 @@ openfft_plan_t openfft_plan(int Na, int Nb, int Nc, int P, int dtype)
         build_transpose_tables(T.t, T.C, sb, rb, ch, 8192, &sd, &rd);
         T.nchunks = (int64_t)ch.size() / 3;
         const size_t pp = sb.size() * sizeof(int64_t);
-        if (cudaMalloc(&T.d_sbase, pp) || cudaMalloc(&T.d_rbase, pp) ||
-            cudaMalloc(&T.d_chunks, ch.size() * sizeof(int64_t) + 8) ||
-            cudaMalloc(&T.d_C, pp) || cudaMalloc(&T.d_sdispl, pp) || cudaMalloc(&T.d_rdispl, pp)) {
+        if (dev_malloc((void**)&T.d_sbase, pp) || dev_malloc((void**)&T.d_rbase, pp) ||
+            dev_malloc((void**)&T.d_chunks, ch.size() * sizeof(int64_t) + 8) ||
+            dev_malloc((void**)&T.d_C, pp) || dev_malloc((void**)&T.d_sdispl, pp) || dev_malloc((void**)&T.d_rdispl, pp)) {
             cudaGetLastError();
             fail(OPENFFT_ERR_NOMEM, "transpose table allocation failed");
             free_plan(p);
@@ -737,7 +764,7 @@ openfft_plan_t openfft_plan(int Na, int Nb, int Nc, int P, int dtype)
         cudaMemcpy(T.d_sdispl, sd.data(), pp, cudaMemcpyHostToDevice);
         cudaMemcpy(T.d_rdispl, rd.data(), pp, cudaMemcpyHostToDevice);
     }
-    if (cudaMalloc(&p->d_status, sizeof(int)) || cudaMemset(p->d_status, 0, sizeof(int))) {
+    if (dev_malloc((void**)&p->d_status, sizeof(int)) || cudaMemset(p->d_status, 0, sizeof(int))) {
         cudaGetLastError();
         fail(OPENFFT_ERR_NOMEM, "status word");
         free_plan(p);
@@ -970,7 +997,7 @@ int exec_host(openfft_plan_t plan, const void* host_in, void* host_out, int dir,
     if (dir != OPENFFT_FORWARD && dir != OPENFFT_BACKWARD) return fail(OPENFFT_ERR_INVALID_ARG, "dir must be -1 or +1");
     const size_t bytes = (size_t)plan->N * plan->elem_bytes;
     if (!plan->stage_in) {
-        if (cudaMalloc(&plan->stage_in, bytes) || cudaMalloc(&plan->stage_out, bytes)) {
+        if (dev_malloc((void**)&plan->stage_in, bytes) || dev_malloc((void**)&plan->stage_out, bytes)) {
             cudaGetLastError();
             cudaFree(plan->stage_in); plan->stage_in = nullptr;
             return fail(OPENFFT_ERR_NOMEM, "staging allocation failed");

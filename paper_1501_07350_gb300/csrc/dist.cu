@@ -241,7 +241,7 @@ void free_dist(openfft_dist_plan_s* p)
 
 int upload(int64_t** dst, const std::vector<int64_t>& v)
 {
-    if (cudaMalloc(dst, sizeof(int64_t) * std::max<size_t>(1, v.size()))) { cudaGetLastError(); return 1; }
+    if (dev_malloc((void**)dst, sizeof(int64_t) * std::max<size_t>(1, v.size()))) { cudaGetLastError(); return 1; }
     return cudaMemcpy(*dst, v.data(), sizeof(int64_t) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess;
 }
 
@@ -330,7 +330,7 @@ openfft_dist_plan_t openfft_dist_plan(int Na, int Nb, int Nc, int P, int G, int 
     const int lens[3] = {Na, Nb, Nc};
     const int twf = p->arith == ARITH_F32 ? FMT_C64 : FMT_DF;
     for (int ax = 0; ax < 3; ++ax) {
-        if (cudaMalloc(&p->tw[ax], twiddle_bytes(lens[ax], twf))) {
+        if (dev_malloc((void**)&p->tw[ax], twiddle_bytes(lens[ax], twf))) {
             cudaGetLastError();
             set_last_error(OPENFFT_ERR_NOMEM, "twiddle allocation failed");
             free_dist(p);

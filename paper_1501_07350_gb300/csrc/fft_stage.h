@@ -56,6 +56,10 @@ enum { KERNEL_R2C = 4, KERNEL_C2R = 5 };
 cudaError_t launch_real_stage(const StageLaunch& L, cudaStream_t st);
 
 cudaError_t stage_kernels_init(int max_dyn_smem);
+// Device allocation of the library's workspaces (capi.cu): cudaMalloc, except
+// that a test control (openfft_debug_alloc_fail) can make the n-th call fail
+// as if the device were out of memory.
+cudaError_t dev_malloc(void** ptr, size_t bytes);
 // Resident CTAs per SM of a persistent kernel with `threads` threads and
 // `dyn_smem` bytes of dynamic shared memory, from the kernel's own limits
 // (shared memory with the whole carveout as shared memory, registers,

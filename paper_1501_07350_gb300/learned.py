@@ -12,6 +12,7 @@ the learned pick avoids.
 Usage (on a GPU machine):
     python -m paper_1501_07350_gb300.learned collect --out timings.json
     python -m paper_1501_07350_gb300.learned train --data timings.json --out model.json
+    python -m paper_1501_07350_gb300.learned families --data timings.json
 """
 from __future__ import annotations
 
@@ -263,6 +264,9 @@ def main(argv=None):
     t.add_argument("--data", default=TIMINGS_FILE)
     t.add_argument("--out", default=MODEL_FILE)
     t.add_argument("--steps", type=int, default=8000)
+    f = sub.add_parser("families")
+    f.add_argument("--data", default=TIMINGS_FILE)
+    f.add_argument("--steps", type=int, default=8000)
     args = ap.parse_args(argv)
     if args.cmd == "collect":
         import torch
@@ -272,6 +276,10 @@ def main(argv=None):
         rows = collect(probs, stream=torch.cuda.current_stream(), log=lambda m: print(m, file=sys.stderr))
         save({"device": torch.cuda.get_device_name(0), "rows": rows}, args.out)
         print(args.out)
+    elif args.cmd == "families":
+        fam = evaluate_families(load_rows(args.data), steps=args.steps)
+        print(json.dumps({k: {"train_problems": v["train_problems"], "summary": v["summary"],
+                              "regrets": [round(e["regret"], 4) for e in v["problems"]]} for k, v in fam.items()}))
     else:
         rows = load_rows(args.data)
         tr, te = split(rows)

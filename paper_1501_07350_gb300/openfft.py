@@ -45,7 +45,8 @@ EXPORTS = [
     "openfft_num_features", "openfft_candidate_features", "openfft_tune_times", "openfft_set_cost_model",
     "openfft_tc_gemm", "openfft_exec_r2c", "openfft_exec_c2r", "openfft_tc_debug", "openfft_set_host_chunks",
     "openfft_exec_c2c_host_async", "openfft_set_copy_streams",
-    "openfft_dist_rows", "openfft_dist_counts", "openfft_dist_pack_host", "openfft_dist_unpack_host",
+    "openfft_debug_alloc_fail", "openfft_nd_plan", "openfft_nd_exec", "openfft_nd_destroy", "openfft_nd_set_stream",
+    "openfft_nd_box", "openfft_nd_decomp_box", "openfft_nd_decomp_counts", "openfft_dist_rows", "openfft_dist_counts", "openfft_dist_pack_host", "openfft_dist_unpack_host",
     "openfft_dist_plan", "openfft_dist_destroy", "openfft_dist_set_stream", "openfft_dist_elem_bytes",
     "openfft_dist_exchange_counts", "openfft_dist_stage", "openfft_dist_pack", "openfft_dist_unpack",
 ]
@@ -119,6 +120,14 @@ def load():
             "openfft_tune_times": (i32, [vp, pf]),
             "openfft_set_cost_model": (i32, [i32, i32, i32, pf]),
             "openfft_tc_gemm": (i32, [i32, i32, i32, i32, i32, pf, pf, pf]),
+            "openfft_debug_alloc_fail": (i32, [ctypes.c_longlong]),
+            "openfft_nd_plan": (vp, [i32, pi32, i32, i32]),
+            "openfft_nd_exec": (i32, [vp, vp, vp, i32]),
+            "openfft_nd_destroy": (None, [vp]),
+            "openfft_nd_set_stream": (i32, [vp, vp]),
+            "openfft_nd_box": (i32, [vp, i32, i32, p64, p64]),
+            "openfft_nd_decomp_box": (i32, [i32, pi32, i32, i32, i32, p64, p64]),
+            "openfft_nd_decomp_counts": (i32, [i32, pi32, i32, i32, p64]),
             "openfft_dist_rows": (i32, [i32, i32, i32, i32, i32, i32, i32, p64, p64]),
             "openfft_dist_counts": (i32, [i32, i32, i32, i32, i32, i32, p64]),
             "openfft_dist_pack_host": (i32, [i32, i32, i32, i32, i32, i32, i32, i32, vp, vp]),
@@ -294,6 +303,57 @@ def openfft_exec_c2c_noalloc(Na: int, Nb: int, Nc: int, P: int, dtype: int, inp,
     """Plan-free transform that allocates nothing (static device scratch, 16 MiB)."""
     raw = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     _check(load().openfft_exec_c2c_noalloc(Na, Nb, Nc, P, dtype, _ptr(inp), _ptr(out), direction, raw))
+
+
+def openfft_debug_alloc_fail(nth: int) -> None:
+    """Test control: the nth device allocation from now on fails (0 = off)."""
+    _check(load().openfft_debug_alloc_fail(nth))
+
+
+# ------------------------------------------------- 4-D and 5-D transforms --
+
+def _dims32(dims):
+    return (ctypes.c_int * len(dims))(*[int(v) for v in dims])
+
+
+def openfft_nd_plan(dims, P: int, dtype: int) -> int:
+    h = load().openfft_nd_plan(len(dims), _dims32(dims), P, dtype)
+    if not h:
+        raise OpenFFTError(load().openfft_last_status(), last_error())
+    return h
+
+
+def openfft_nd_exec(plan: int, inp, out, direction: int) -> None:
+    _check(load().openfft_nd_exec(plan, _ptr(inp), _ptr(out), direction))
+
+
+def openfft_nd_destroy(plan: int) -> None:
+    load().openfft_nd_destroy(plan)
+
+
+def openfft_nd_set_stream(plan: int, stream) -> None:
+    raw = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(load().openfft_nd_set_stream(plan, raw))
+
+
+def openfft_nd_box(plan: int, which: int, rank: int):
+    off, cnt = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().openfft_nd_box(plan, which, rank, ctypes.byref(off), ctypes.byref(cnt)))
+    return off.value, cnt.value
+
+
+def openfft_nd_decomp_box(dims, P: int, ordering: int, rank: int):
+    off, cnt = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().openfft_nd_decomp_box(len(dims), _dims32(dims), P, ordering, rank, ctypes.byref(off),
+                                        ctypes.byref(cnt)))
+    return off.value, cnt.value
+
+
+def openfft_nd_decomp_counts(dims, P: int, exchange: int) -> np.ndarray:
+    out = np.zeros((P, P), dtype=np.int64)
+    _check(load().openfft_nd_decomp_counts(len(dims), _dims32(dims), P, exchange,
+                                           out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return out
 
 
 # ------------------------------------------- transform over several devices --

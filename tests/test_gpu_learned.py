@@ -7,7 +7,9 @@ the LEARNED tuning mode, and the regret of the trained cost model.
 - OPENFFT_TUNE_LEARNED picks a candidate of the lowest predicted time;
 - trained on the committed timing dataset, the model's picks on the held-out
   problems (the benchmark configurations) are within 5 % of exhaustive tuning
-  on average, and avoid the exhaustive tuning time.
+  on average, and avoid the exhaustive tuning time;
+- trained without any problem that has a 512-point axis, its picks on the
+  512^3 benchmark problems are within 5 % of exhaustive tuning too.
 """
 import os
 
@@ -107,6 +109,13 @@ def test_trained_model_regret_on_held_out_problems(lib):
     assert s["mean_regret"] <= 0.05, s
     assert s["geomean_speedup_vs_default"] >= 0.97, s
     assert s["tuning_cost_avoided_ms"] > 0
+    # family hold-out: no training problem with a 512-point axis when the 512^3
+    # benchmark problems are evaluated (the headline configuration)
+    fam = learned.evaluate_families(rows)
+    f512 = fam["512-point axes"]
+    assert f512["summary"]["problems"] == 5
+    assert f512["summary"]["mean_regret"] <= 0.05, f512["summary"]
+    assert fam["axes with a factor 3 or 5"]["summary"]["problems"] == 2
     # the committed ensemble, installed, drives OPENFFT_TUNE_LEARNED
     learned.install()
     try:
