@@ -70,7 +70,8 @@ enum {
     OPENFFT_ERR_NOMEM = 5,             /* device allocation failed (plan time, or the first host-buffer call) */
     OPENFFT_ERR_TIMEOUT = 6,           /* a bounded device wait ran out (batched kernel)    */
     OPENFFT_ERR_ALIAS = 7,             /* in == out                                         */
-    OPENFFT_ERR_UNSUPPORTED = 8        /* the request is valid but this build does not do it */
+    OPENFFT_ERR_UNSUPPORTED = 8,       /* the request is valid but this build does not do it */
+    OPENFFT_ERR_BOUNDS = 9             /* checked build only: a kernel met a global index outside its array */
 };
 
 /* Transpose variants: the paper's six communication methods (Sec. 3.2.1),
@@ -387,6 +388,24 @@ int openfft_tc_debug(int what, long long value);
  * switches it off; it switches itself off after the failure.  INVALID_ARG
  * for nth < 0.  Not thread-safe with concurrent plan creation. */
 int openfft_debug_alloc_fail(long long nth);
+
+/* The checked build (compiled with -DOPENFFT_CHECKED; the library of the same
+ * ABI under another file name) tests every global element index of the C2C
+ * stage kernels (all forms), of the explicit transposes (pack, exchange,
+ * unpack, the stepped exchanges) and of the multi-device pack / unpack
+ * against the length of the array it addresses.  An index outside it is not
+ * accessed, and OPENFFT_ERR_BOUNDS is stored in a device status word: the
+ * plan's, reported by openfft_sync, or, for calls without one (D-dimensional,
+ * multi-device and allocation-free calls), a word per device that
+ * openfft_debug_bounds_status reads.  Nothing traps.  The real-to-complex,
+ * batched and tensor-core stage kernels are not checked.
+ * openfft_checked_build returns 1 in that build, 0 otherwise. */
+int openfft_checked_build(void);
+
+/* Checked build: synchronises the device, stores in *status the per-device
+ * bounds status word (OPENFFT_OK or OPENFFT_ERR_BOUNDS) and clears it.  Other
+ * builds: *status = OPENFFT_OK and the call returns OPENFFT_ERR_UNSUPPORTED. */
+int openfft_debug_bounds_status(int* status);
 
 /* ------------------------------------------- over several devices ----- */
 

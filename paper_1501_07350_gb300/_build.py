@@ -16,6 +16,9 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_NAME = "libopenfft_gb.so"
 LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
+# the bounds-checked build (-DOPENFFT_CHECKED): same ABI, its own folder and name
+CHECKED_DIR = os.path.join(HERE, "_build_checked")
+CHECKED_LIB_PATH = os.path.join(CHECKED_DIR, "libopenfft_gb_checked.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["capi.cu", "fft_stage.cu", "redistribute.cu", "fft_tile_f64.cu", "fft_tile_df.cu", "fft_tile_f32.cu", "noalloc.cu", "batch.cu", "mlp.cu", "tcgemm.cu", "dftgemm.cu", "r2c.cu", "dist.cu", "fft_tma_256.cu", "fft_tma_512.cu", "nd.cu"]
@@ -38,23 +41,27 @@ def _inputs():
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB_PATH):
+def up_to_date(lib: str = LIB_PATH) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB_PATH)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile every CUDA source for sm_103a and link the shared library."""
-    if not force and up_to_date():
-        return LIB_PATH
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), checked: bool = False) -> str:
+    """Compile every CUDA source for sm_103a and link the shared library
+    (checked=True: the bounds-checked library, compiled with -DOPENFFT_CHECKED)."""
+    out_dir, lib_path = (CHECKED_DIR, CHECKED_LIB_PATH) if checked else (OUT_DIR, LIB_PATH)
+    if checked:
+        extra_flags = ["-DOPENFFT_CHECKED", *extra_flags]
+    if not force and up_to_date(lib_path):
+        return lib_path
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
     objs = []
     cmds = []
     for src in SOURCES:
-        obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(out_dir, src.replace(".cu", ".o"))
         objs.append(obj)
         cmds.append([nvcc, *ARCH, *FLAGS, *extra_flags, "-c", os.path.join(CSRC, src), "-o", obj])
 
@@ -72,13 +79,12 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         for lg in logs:
             if lg:
                 print(lg, file=sys.stderr)
-    tmp = LIB_PATH + ".%d.tmp" % os.getpid()
+    tmp = lib_path + ".%d.tmp" % os.getpid()
     run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True,
-          extra_flags=["-Xptxas", "-v"] if "--ptxas-v" in sys.argv else [])
-    print(LIB_PATH)
+    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv,
+                extra_flags=["-Xptxas", "-v"] if "--ptxas-v" in sys.argv else []))

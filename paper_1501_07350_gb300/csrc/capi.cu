@@ -222,6 +222,7 @@ int make_stage(openfft_plan_s* p, int axis, int arith, int Gt, int family, int64
     L.arith = arith;
     L.sms = p->sms;
     L.family = family;
+    L.status = p->d_status;
     L.grid = a.ngroups * (group_i2 ? M1 : M2);
     L.smem = 2 * (size_t)n * (G + 1) * E;     // two ping-pong tiles
     if (L.grid > 0x7fffffffLL) return fail(OPENFFT_ERR_UNSUPPORTED, "grid too large");
@@ -461,6 +462,8 @@ int run_ops(openfft_plan_s* p, const std::vector<Op>& ops, const void* in, void*
         int st = record(p, -1);
         if (st) return st;
     }
+    Bounds bnd;                   // every buffer of a transpose holds N elements
+    bnd.chk = p->d_status; bnd.lim = p->N;
     for (size_t i = i0; i < i1; ++i) {
         const Op& o = ops[i];
         void* s = resolve(p, o.src, in, out);
@@ -472,15 +475,15 @@ int run_ops(openfft_plan_s* p, const std::vector<Op>& ops, const void* in, void*
             e = launch_stage(L, p->stream);
         } else if (o.kind == OP_SEG_EXCHANGE) {
             const TransposeTables& T = p->tt[o.tix];
-            e = launch_segment_exchange(o.sched, p->P, kBlockSize, o.step, E, T.d_C, T.d_sdispl, T.d_rdispl, s, d, p->stream);
+            e = launch_segment_exchange(o.sched, p->P, kBlockSize, o.step, E, T.d_C, T.d_sdispl, T.d_rdispl, s, d, p->stream, bnd);
         } else if (o.kind == OP_SEG_UNPACK) {
             const TransposeTables& T = p->tt[o.tix];
-            e = launch_segment_unpack(T.t, o.sched, kBlockSize, o.step, E, s, d, T.d_sbase, p->stream);
+            e = launch_segment_unpack(T.t, o.sched, kBlockSize, o.step, E, s, d, T.d_sbase, p->stream, bnd);
         } else {
             const TransposeTables& T = p->tt[o.tix];
-            if (o.kind == OP_PACK) e = launch_pack(T.t, E, s, d, T.d_sbase, p->N, p->sms, p->stream);
-            else if (o.kind == OP_EXCHANGE) e = launch_exchange(E, T.d_chunks, T.nchunks, s, d, p->sms, p->stream);
-            else e = launch_unpack(T.t, E, s, d, o.from_send ? T.d_sbase : T.d_rbase, o.from_send, p->N, p->sms, p->stream);
+            if (o.kind == OP_PACK) e = launch_pack(T.t, E, s, d, T.d_sbase, p->N, p->sms, p->stream, bnd);
+            else if (o.kind == OP_EXCHANGE) e = launch_exchange(E, T.d_chunks, T.nchunks, s, d, p->sms, p->stream, bnd);
+            else e = launch_unpack(T.t, E, s, d, o.from_send ? T.d_sbase : T.d_rbase, o.from_send, p->N, p->sms, p->stream, bnd);
         }
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
         if (p->timing) {
@@ -641,6 +644,32 @@ int openfft_debug_alloc_fail(long long nth)
     if (nth < 0) return fail(OPENFFT_ERR_INVALID_ARG, "nth must be >= 0");
     g_alloc_fail_at.store(nth);
     return OPENFFT_OK;
+}
+
+int openfft_debug_bounds_status(int* status)
+{
+    if (!status) return fail(OPENFFT_ERR_INVALID_ARG, "null status");
+    *status = OPENFFT_OK;
+#ifdef OPENFFT_CHECKED
+    int* w = fallback_status_word();
+    if (!w) return fail(OPENFFT_ERR_CUDA, "status word of the checked build");
+    cudaError_t e;
+    if ((e = cudaDeviceSynchronize()) || (e = cudaMemcpy(status, w, sizeof(int), cudaMemcpyDeviceToHost)) ||
+        (e = cudaMemset(w, 0, sizeof(int))))
+        return cuda_fail(e, "status word of the checked build");
+    return OPENFFT_OK;
+#else
+    return fail(OPENFFT_ERR_UNSUPPORTED, "not the checked build (OPENFFT_CHECKED)");
+#endif
+}
+
+int openfft_checked_build(void)
+{
+#ifdef OPENFFT_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 int openfft_decomp_degree(int Na, int Nb, int Nc, int P, int layout)
@@ -890,6 +919,7 @@ StageLaunch stage_lines(const StageLaunch& L, int64_t u0, int64_t u1, int64_t* i
 {
     StageLaunch c = L;
     StageArgs& a = c.args;
+    const int64_t whole = a.M1 * a.M2 * (int64_t)a.n;
     if (a.M2 > 1) {
         *in_off = u0 * a.M1 * a.n; *out_off = u0 * a.S2; *lines = (u1 - u0) * a.M1;
         a.M2 = u1 - u0;
@@ -899,6 +929,8 @@ StageLaunch stage_lines(const StageLaunch& L, int64_t u0, int64_t u1, int64_t* i
     }
     const int64_t Mg = a.group_i2 ? a.M2 : a.M1;
     a.ngroups = (Mg + a.G - 1) / a.G;
+    a.in_elems = (a.in_elems ? a.in_elems : whole) - *in_off;
+    a.out_elems = (a.out_elems ? a.out_elems : whole) - *out_off;
     c.grid = a.ngroups * (a.group_i2 ? a.M1 : a.M2);
     return c;
 }
@@ -1125,7 +1157,8 @@ int openfft_sync(openfft_plan_t plan)
         if ((e = cudaMemcpy(&st, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost))) return cuda_fail(e, "status word");
         if (st) {
             cudaMemset(plan->d_status, 0, sizeof(int));
-            return fail(st, "a bounded tensor-core completion wait ran out");
+            return fail(st, st == OPENFFT_ERR_BOUNDS ? "a global index outside its array (checked build)"
+                                                     : "a bounded tensor-core completion wait ran out");
         }
     }
     return OPENFFT_OK;
@@ -1347,15 +1380,17 @@ int openfft_redistribute(openfft_plan_t plan, int exchange, int variant, const v
         // the ops of one transpose: send segments in A, receive buffers in B
         std::vector<Op> ops;
         transpose_ops(ops, variant, tix_of(exchange), B_B, B_OUT, plan->P);
+        Bounds bnd;
+        bnd.chk = plan->d_status; bnd.lim = plan->N;
         for (const Op& o : ops) {
             const void* src = o.src == B_IN ? in : (o.src == B_OUT ? out : (o.src == B_A ? plan->bufA : plan->bufB));
             void* dst = o.dst == B_OUT ? out : (o.dst == B_A ? plan->bufA : plan->bufB);
             if (o.kind == OP_PACK) src = in;                 // the source ordering is the caller's input
-            if (o.kind == OP_PACK) e = launch_pack(T.t, E, src, dst, T.d_sbase, plan->N, plan->sms, plan->stream);
-            else if (o.kind == OP_EXCHANGE) e = launch_exchange(E, T.d_chunks, T.nchunks, src, dst, plan->sms, plan->stream);
-            else if (o.kind == OP_UNPACK) e = launch_unpack(T.t, E, src, dst, o.from_send ? T.d_sbase : T.d_rbase, o.from_send, plan->N, plan->sms, plan->stream);
-            else if (o.kind == OP_SEG_EXCHANGE) e = launch_segment_exchange(o.sched, plan->P, kBlockSize, o.step, E, T.d_C, T.d_sdispl, T.d_rdispl, src, dst, plan->stream);
-            else e = launch_segment_unpack(T.t, o.sched, kBlockSize, o.step, E, src, dst, T.d_sbase, plan->stream);
+            if (o.kind == OP_PACK) e = launch_pack(T.t, E, src, dst, T.d_sbase, plan->N, plan->sms, plan->stream, bnd);
+            else if (o.kind == OP_EXCHANGE) e = launch_exchange(E, T.d_chunks, T.nchunks, src, dst, plan->sms, plan->stream, bnd);
+            else if (o.kind == OP_UNPACK) e = launch_unpack(T.t, E, src, dst, o.from_send ? T.d_sbase : T.d_rbase, o.from_send, plan->N, plan->sms, plan->stream, bnd);
+            else if (o.kind == OP_SEG_EXCHANGE) e = launch_segment_exchange(o.sched, plan->P, kBlockSize, o.step, E, T.d_C, T.d_sdispl, T.d_rdispl, src, dst, plan->stream, bnd);
+            else e = launch_segment_unpack(T.t, o.sched, kBlockSize, o.step, E, src, dst, T.d_sbase, plan->stream, bnd);
             if (e) break;
         }
     } else {

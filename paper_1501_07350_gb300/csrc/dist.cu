@@ -175,28 +175,30 @@ template <class E>
 __global__ void dist_pack_kernel(const Transpose t, int64_t P, int64_t G, int64_t R0, int64_t n,
                                  const int64_t* __restrict__ q0, const int64_t* __restrict__ q1,
                                  const int64_t* __restrict__ sdispl, const int64_t* __restrict__ spre,
-                                 const E* __restrict__ src, E* __restrict__ send)
+                                 const E* __restrict__ src, E* __restrict__ send, const Bounds b)
 {
     const int64_t Ls = row_len(t), Ld = dst_row_len(t);
     for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = R0 + x / Ls, e = x % Ls;
         const int64_t y = dest_index(t, q, e);
         const int64_t h = device_of(P, G, row_owner(t.dst, y / Ld));
-        send[pack_pos(t, q, e, q0[h], q1[h], sdispl[h], spre[h])] = src[x];
+        const int64_t pos = pack_pos(t, q, e, q0[h], q1[h], sdispl[h], spre[h]);
+        if (in_bounds(b, pos)) send[pos] = src[x];
     }
 }
 
 template <class E>
 __global__ void dist_unpack_kernel(const Transpose t, int64_t P, int64_t G, int64_t Q0, int64_t Q1, int64_t n,
                                    const int64_t* __restrict__ rdispl, const int64_t* __restrict__ rpre,
-                                   const E* __restrict__ recv, E* __restrict__ dst)
+                                   const E* __restrict__ recv, E* __restrict__ dst, const Bounds b)
 {
     const int64_t Ld = dst_row_len(t);
     for (int64_t yl = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; yl < n; yl += (int64_t)gridDim.x * blockDim.x) {
         int64_t q, e;
         source_of(t, Q0 * Ld + yl, &q, &e);
         const int64_t g = device_of(P, G, row_owner(t.src, q));
-        dst[yl] = recv[pack_pos(t, q, e, Q0, Q1, rdispl[g], rpre[g])];
+        const int64_t pos = pack_pos(t, q, e, Q0, Q1, rdispl[g], rpre[g]);
+        if (in_bounds(b, pos)) dst[yl] = recv[pos];
     }
 }
 
@@ -446,12 +448,14 @@ int openfft_dist_pack(openfft_dist_plan_t p, int exchange, const void* src, void
     const int64_t n = (d.R1 - d.R0) * row_len(d.t);
     if (n == 0) return OPENFFT_OK;
     const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)p->sms * 8);
+    Bounds bnd;                                  // the send buffer holds this device's n elements
+    bnd.chk = fallback_status_word(); bnd.lim = n;
     if (p->arith == ARITH_F32)
         dist_pack_kernel<float2><<<grid, 256, 0, p->stream>>>(d.t, p->P, p->G, d.R0, n, t.q0, t.q1, t.sdispl, t.spre,
-                                                             static_cast<const float2*>(src), static_cast<float2*>(send));
+                                                             static_cast<const float2*>(src), static_cast<float2*>(send), bnd);
     else
         dist_pack_kernel<double2><<<grid, 256, 0, p->stream>>>(d.t, p->P, p->G, d.R0, n, t.q0, t.q1, t.sdispl, t.spre,
-                                                              static_cast<const double2*>(src), static_cast<double2*>(send));
+                                                              static_cast<const double2*>(src), static_cast<double2*>(send), bnd);
     cudaError_t e = cudaGetLastError();
     return e ? set_last_error(OPENFFT_ERR_CUDA, cudaGetErrorString(e)) : OPENFFT_OK;
 }
@@ -467,12 +471,14 @@ int openfft_dist_unpack(openfft_dist_plan_t p, int exchange, const void* recv, v
     const int64_t n = (d.Q1 - d.Q0) * dst_row_len(d.t);
     if (n == 0) return OPENFFT_OK;
     const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)p->sms * 8);
+    Bounds bnd;                                  // the receive buffer holds this device's n elements
+    bnd.chk = fallback_status_word(); bnd.lim = n;
     if (p->arith == ARITH_F32)
         dist_unpack_kernel<float2><<<grid, 256, 0, p->stream>>>(d.t, p->P, p->G, d.Q0, d.Q1, n, t.rdispl, t.rpre,
-                                                               static_cast<const float2*>(recv), static_cast<float2*>(dst));
+                                                               static_cast<const float2*>(recv), static_cast<float2*>(dst), bnd);
     else
         dist_unpack_kernel<double2><<<grid, 256, 0, p->stream>>>(d.t, p->P, p->G, d.Q0, d.Q1, n, t.rdispl, t.rpre,
-                                                                static_cast<const double2*>(recv), static_cast<double2*>(dst));
+                                                                static_cast<const double2*>(recv), static_cast<double2*>(dst), bnd);
     cudaError_t e = cudaGetLastError();
     return e ? set_last_error(OPENFFT_ERR_CUDA, cudaGetErrorString(e)) : OPENFFT_OK;
 }

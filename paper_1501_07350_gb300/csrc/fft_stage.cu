@@ -135,8 +135,31 @@ cudaError_t stage_kernels_init(int max_dyn_smem)
     return cudaFuncSetAttribute(fft_stage_kernel<ArDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem);
 }
 
-cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st)
+#ifdef OPENFFT_CHECKED
+__device__ int g_bounds_status;       // status word of launches whose plan has none
+#endif
+
+int* fallback_status_word()
 {
+#ifdef OPENFFT_CHECKED
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_bounds_status) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return static_cast<int*>(ptr);
+#else
+    return nullptr;
+#endif
+}
+
+cudaError_t launch_stage(const StageLaunch& L0, cudaStream_t st)
+{
+    StageLaunch L = L0;
+    const int64_t elems = L.args.M1 * L.args.M2 * (int64_t)L.args.n;
+    if (!L.args.in_elems) L.args.in_elems = elems;
+    if (!L.args.out_elems) L.args.out_elems = elems;
+    if (!L.args.chk) L.args.chk = L.status ? L.status : fallback_status_word();
     if (L.family == KERNEL_R2C || L.family == KERNEL_C2R) return launch_real_stage(L, st);
     if (L.arith == ARITH_TC_TF32 || L.arith == ARITH_TC_BF16) return launch_dftgemm(L, st, L.status);
     bool handled = false;

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include "checked.h"
 
 namespace ofg {
 
@@ -35,7 +36,13 @@ struct StageArgs {
     int radix[kMaxPasses];
     int conj_in, conj_out, do_fft;
     int in_fmt, out_fmt;
+    // elements of the arrays that in and out point into, counted from those
+    // pointers (launch_stage fills in M1 M2 n when left 0), and the status
+    // word of the bounds checks; read only by the checked build (checked.h)
+    int64_t in_elems, out_elems;
+    int* chk;
 };
+
 
 struct StageLaunch {
     StageArgs args;

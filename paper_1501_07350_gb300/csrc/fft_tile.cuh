@@ -171,8 +171,12 @@ __device__ __forceinline__ void tile_issue_loads(const StageArgs& p, const TileG
             C* dst = buf + slot_of<N, G>(e);
             const char* src = tg.lstride == 1 ? first + (int64_t)e * EB
                                               : first + g * gstride + (e - g * N) * EB;
-            if (g < tg.valid) cp_async<EB>(dst, src);
-            else *dst = A::zero();
+            const int64_t idx = tg.line0 * N + (tg.lstride == 1 ? (int64_t)e : g * tg.lstride * N + (e - g * N));
+            if (g < tg.valid) {
+                if (in_bounds(p.chk, idx, p.in_elems)) cp_async<EB>(dst, src);
+            } else {
+                *dst = A::zero();
+            }
         }
     }
     cp_async_commit();
@@ -228,7 +232,8 @@ __device__ __forceinline__ void tile_store(const StageArgs& p, const TileGeom& t
         const int64_t step = (int64_t)(T / G) * p.Sk * EB;
 #pragma unroll 4
         for (int k = slot; k < N; k += T / G) {
-            put<A, CONJ_SCALE, EXT>(ptr, buf[k * (G + 1) + g], p.scale);
+            if (in_bounds(p.chk, tg.obase + g * tg.ostride + (int64_t)k * p.Sk, p.out_elems))
+                put<A, CONJ_SCALE, EXT>(ptr, buf[k * (G + 1) + g], p.scale);
             ptr += step;
         }
     } else {
@@ -236,7 +241,7 @@ __device__ __forceinline__ void tile_store(const StageArgs& p, const TileGeom& t
 #pragma unroll
         for (int it = 0; it < ITERS; ++it) {
             const int e = tid + it * T;
-            if ((TOTAL % T == 0 || e < TOTAL) && e / N < tg.valid)
+            if ((TOTAL % T == 0 || e < TOTAL) && e / N < tg.valid && in_bounds(p.chk, tg.obase + e, p.out_elems))
                 put<A, CONJ_SCALE, EXT>(first + (int64_t)e * EB, buf[slot_of<N, G>(e)], p.scale);
         }
     }

@@ -115,7 +115,8 @@ __device__ __forceinline__ void warp_issue_load(const StageArgs& p, const TileGe
 #pragma unroll
         for (int u = 0; u < N / 32; ++u) {
             const int pos = lane + 32 * u;
-            cp_async<EB>(line + wpad<sizeof(typename A::C)>(pos), src + pos * EB);
+            if (in_bounds(p.chk, (tg.line0 + g * tg.lstride) * N + pos, p.in_elems))
+                cp_async<EB>(line + wpad<sizeof(typename A::C)>(pos), src + pos * EB);
         }
     } else {
 #pragma unroll
@@ -157,7 +158,8 @@ __device__ __forceinline__ void warp_tile_store(const StageArgs& p, const TileGe
         const int64_t step = (int64_t)SL * p.Sk * EB;
 #pragma unroll 4
         for (int k = slot; k < N; k += SL) {
-            put<A, CONJ_SCALE, EXT>(ptr, line[wpad<CB>(k)], p.scale);
+            if (in_bounds(p.chk, tg.obase + g * tg.ostride + (int64_t)k * p.Sk, p.out_elems))
+                put<A, CONJ_SCALE, EXT>(ptr, line[wpad<CB>(k)], p.scale);
             ptr += step;
         }
     } else {
@@ -172,7 +174,8 @@ __device__ __forceinline__ void warp_tile_store(const StageArgs& p, const TileGe
 #pragma unroll
             for (int u = 0; u < N / 32; ++u) {
                 const int k = lane + 32 * u;
-                put<A, CONJ_SCALE, EXT>(ptr + k * EB, line[wpad<CB>(k)], p.scale);
+                if (in_bounds(p.chk, tg.obase + (int64_t)g * tg.ostride + k, p.out_elems))
+                    put<A, CONJ_SCALE, EXT>(ptr + k * EB, line[wpad<CB>(k)], p.scale);
             }
         }
     }

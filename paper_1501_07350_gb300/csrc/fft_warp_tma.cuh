@@ -198,7 +198,8 @@ __device__ __forceinline__ void tma_issue_load(const StageArgs& p, const TileGeo
 #pragma unroll
         for (int u = 0; u < N / (32 * WPL); ++u) {
             const int pos = lane + 32 * (w + WPL * u);
-            cp_async<16>(line + wpad<16>(pos), src + pos * 16);
+            if (in_bounds(p.chk, (tg.line0 + g * tg.lstride) * N + pos, p.in_elems))
+                cp_async<16>(line + wpad<16>(pos), src + pos * 16);
         }
     } else {
 #pragma unroll
@@ -293,7 +294,10 @@ fft_warp_tma_kernel(const StageArgs p, int64_t ntiles, const __grid_constant__ C
             } else {
                 char* first = reinterpret_cast<char*>(p.out) + tg.obase * 16;
                 for (int gg = 0; gg < tg.valid; ++gg)
-                    bulk_store(first + (int64_t)gg * tg.ostride * 16, smem_addr(stage) + (uint32_t)gg * N * 16u, N * 16u);
+                    if (in_bounds(p.chk, tg.obase + gg * tg.ostride, p.out_elems) &&
+                        in_bounds(p.chk, tg.obase + gg * tg.ostride + N - 1, p.out_elems))
+                        bulk_store(first + (int64_t)gg * tg.ostride * 16, smem_addr(stage) + (uint32_t)gg * N * 16u,
+                                   N * 16u);
             }
             bulk_commit();
         }
@@ -389,6 +393,20 @@ cudaError_t launch_warp_tma_n(const StageLaunch& L, cudaStream_t st, bool* handl
         *handled = false;
         return cudaSuccess;
     }
+#ifdef OPENFFT_CHECKED
+    // The copy engine clips a tensor store to the map's extent; the checked
+    // build takes this kernel only when that extent lies inside the output
+    // array, and leaves other stages to the per-element checks of the warp
+    // kernel, which report an index outside it.
+    if (!contig) {
+        const int64_t Mg = a.group_i2 ? a.M2 : a.M1, Mo = a.group_i2 ? a.M1 : a.M2;
+        const int64_t So = a.group_i2 ? a.S1 : a.S2;
+        if ((Mg - 1) + (int64_t)(a.n - 1) * a.Sk + (Mo > 1 ? (Mo - 1) * So : 0) >= a.out_elems) {
+            *handled = false;
+            return cudaSuccess;
+        }
+    }
+#endif
     *handled = true;
     const bool ext = a.out_fmt != FMT_DF, cs = a.conj_out != 0;
     if (contig) {

@@ -88,8 +88,11 @@ __device__ __forceinline__ void generic_stage_tile(const StageArgs& p, int64_t c
         for (int e = tid; e < total; e += kStageThreads) {
             const int64_t base = s_in[g];
             C* dst = buf0 + i * ld + g;
-            if (base >= 0) cp_async<EB>(dst, src + (base + i) * EB);
-            else *dst = A::zero();
+            if (base >= 0) {
+                if (in_bounds(p.chk, base + i, p.in_elems)) cp_async<EB>(dst, src + (base + i) * EB);
+            } else {
+                *dst = A::zero();
+            }
             i += di; g += dg;
             if (i >= n) { i -= n; ++g; }
         }
@@ -143,7 +146,7 @@ __device__ __forceinline__ void generic_stage_tile(const StageArgs& p, int64_t c
         int g = tid / n, k = tid - g * n;
         for (int e = tid; e < total; e += kStageThreads) {
             const int64_t base = s_out[g];
-            if (base >= 0) {
+            if (base >= 0 && in_bounds(p.chk, base + k * p.Sk, p.out_elems)) {
                 C v = cur[k * ld + g];
                 if (p.conj_out) v = A::conj(v);
                 if (scale) v = A::scale(v, p.scale);
@@ -156,7 +159,7 @@ __device__ __forceinline__ void generic_stage_tile(const StageArgs& p, int64_t c
         for (int e = tid; e < total; e += kStageThreads) {
             const int k = e >> p.log2G, g = e & (G - 1);
             const int64_t base = s_out[g];
-            if (base < 0) continue;
+            if (base < 0 || !in_bounds(p.chk, base + k * p.Sk, p.out_elems)) continue;
             C v = cur[k * ld + g];
             if (p.conj_out) v = A::conj(v);
             if (scale) v = A::scale(v, p.scale);

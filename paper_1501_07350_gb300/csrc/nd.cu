@@ -344,6 +344,8 @@ int openfft_nd_exec(openfft_nd_plan_t p, const void* in, void* out, int dir)
         StageLaunch L = op.L;
         L.args.in = static_cast<const char*>(bufs_in[op.src]) + op.in_off * (int64_t)E;
         L.args.out = static_cast<char*>(bufs_out[op.dst]) + op.out_off * (int64_t)E;
+        L.args.in_elems = p->N - op.in_off;        // every buffer holds N elements
+        L.args.out_elems = p->N - op.out_off;
         cudaError_t e = launch_stage(L, p->stream);
         if (e) return set_last_error(OPENFFT_ERR_CUDA, cudaGetErrorString(e));
     }

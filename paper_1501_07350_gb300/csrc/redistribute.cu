@@ -20,7 +20,7 @@ namespace ofg {
 
 template <class E>
 __global__ void pack_kernel(const Transpose t, const E* __restrict__ src, E* __restrict__ send,
-                            const int64_t* __restrict__ sbase, int64_t N)
+                            const int64_t* __restrict__ sbase, int64_t N, const Bounds b)
 {
     const int64_t P = t.src.P;
     const int64_t Ls = row_len(t), Ld = dst_row_len(t);
@@ -34,18 +34,19 @@ __global__ void pack_kernel(const Transpose t, const E* __restrict__ src, E* __r
         int64_t e_lo, cnt;
         row_range(t, q, Q0, Q1, &e_lo, &cnt);
         const int64_t pos = sbase[r * P + s] + prefix_to(t, q, Q0, Q1) + (e - e_lo);
-        send[pos] = src[x];
+        if (in_bounds(b, pos)) send[pos] = src[x];
     }
 }
 
 // chunks: (src offset, dst offset, length) triples, one CTA per chunk
 template <class E>
 __global__ void exchange_kernel(const int64_t* __restrict__ chunks, int64_t nchunks,
-                                const E* __restrict__ send, E* __restrict__ recv)
+                                const E* __restrict__ send, E* __restrict__ recv, const Bounds b)
 {
     for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const int64_t so = chunks[3 * c], ro = chunks[3 * c + 1], len = chunks[3 * c + 2];
-        for (int64_t j = threadIdx.x; j < len; j += blockDim.x) recv[ro + j] = send[so + j];
+        for (int64_t j = threadIdx.x; j < len; j += blockDim.x)
+            if (in_bounds(b, so + j) && in_bounds(b, ro + j)) recv[ro + j] = send[so + j];
     }
 }
 
@@ -53,7 +54,7 @@ __global__ void exchange_kernel(const int64_t* __restrict__ chunks, int64_t nchu
 // from_send = 1: buf is the send buffer,    base indexed [r * P + s].
 template <class E>
 __global__ void unpack_kernel(const Transpose t, const E* __restrict__ buf, E* __restrict__ dst,
-                              const int64_t* __restrict__ base, int from_send, int64_t N)
+                              const int64_t* __restrict__ base, int from_send, int64_t N, const Bounds bd)
 {
     const int64_t P = t.src.P;
     const int64_t Ld = dst_row_len(t);
@@ -68,7 +69,7 @@ __global__ void unpack_kernel(const Transpose t, const E* __restrict__ buf, E* _
         row_range(t, q, Q0, Q1, &e_lo, &cnt);
         const int64_t rank = prefix_to(t, q, Q0, Q1) + (e - e_lo);
         const int64_t b = from_send ? base[r * P + s] : base[s * P + r];
-        dst[y] = buf[b + rank];
+        if (in_bounds(bd, b + rank)) dst[y] = buf[b + rank];
     }
 }
 
@@ -114,16 +115,18 @@ template <class E>
 __global__ void segment_exchange_kernel(int sched, int64_t P, int64_t B, int64_t step,
                                         const int64_t* __restrict__ C, const int64_t* __restrict__ sdispl,
                                         const int64_t* __restrict__ rdispl, const E* __restrict__ send,
-                                        E* __restrict__ recv)
+                                        E* __restrict__ recv, const Bounds b)
 {
     int64_t r, s;
     pair_of(sched, P, B, step, blockIdx.x, &r, &s);
     if (s < 0) return;
     const int64_t len = C[r * P + s];
-    const E* src = send + sdispl[r * P + s];
-    E* dst = recv + rdispl[s * P + r];
+    const int64_t so = sdispl[r * P + s], ro = rdispl[s * P + r];
+    const E* src = send + so;
+    E* dst = recv + ro;
     const int64_t stride = (int64_t)gridDim.y * blockDim.x;
-    for (int64_t j = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; j < len; j += stride) dst[j] = src[j];
+    for (int64_t j = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; j < len; j += stride)
+        if (in_bounds(b, so + j) && in_bounds(b, ro + j)) dst[j] = src[j];
 }
 
 // blockIdx.x: pair of the step, blockIdx.y: share of it.  The receiver takes
@@ -134,7 +137,7 @@ __global__ void segment_exchange_kernel(int sched, int64_t P, int64_t B, int64_t
 template <class E>
 __global__ void segment_unpack_kernel(const Transpose t, int sched, int64_t B, int64_t step,
                                       const E* __restrict__ send, E* __restrict__ dst,
-                                      const int64_t* __restrict__ sbase)
+                                      const int64_t* __restrict__ sbase, const Bounds b)
 {
     const int64_t P = t.src.P;
     int64_t r, s;
@@ -149,7 +152,10 @@ __global__ void segment_unpack_kernel(const Transpose t, int sched, int64_t B, i
         row_range(t, q, Q0, Q1, &e_lo, &cnt);
         if (cnt <= 0) continue;
         const int64_t pos = base + prefix_to(t, q, Q0, Q1);
-        for (int64_t e = 0; e < cnt; ++e) dst[dest_index(t, q, e_lo + e)] = send[pos + e];
+        for (int64_t e = 0; e < cnt; ++e) {
+            const int64_t y = dest_index(t, q, e_lo + e);
+            if (in_bounds(b, y) && in_bounds(b, pos + e)) dst[y] = send[pos + e];
+        }
     }
 }
 
@@ -171,26 +177,27 @@ static dim3 step_grid(int64_t pairs)
 
 cudaError_t launch_segment_exchange(int sched, int64_t P, int64_t B, int64_t step, int elem_bytes,
                                     const int64_t* C, const int64_t* sdispl, const int64_t* rdispl,
-                                    const void* send, void* recv, cudaStream_t st)
+                                    const void* send, void* recv, cudaStream_t st, const Bounds& b)
 {
     const dim3 grid = step_grid(pairs_per_step(sched, P, B));
     if (elem_bytes == 16)
         segment_exchange_kernel<uint4><<<grid, 128, 0, st>>>(sched, P, B, step, C, sdispl, rdispl,
-                                                             (const uint4*)send, (uint4*)recv);
+                                                             (const uint4*)send, (uint4*)recv, b);
     else
         segment_exchange_kernel<uint2><<<grid, 128, 0, st>>>(sched, P, B, step, C, sdispl, rdispl,
-                                                             (const uint2*)send, (uint2*)recv);
+                                                             (const uint2*)send, (uint2*)recv, b);
     return cudaGetLastError();
 }
 
 cudaError_t launch_segment_unpack(const Transpose& t, int sched, int64_t B, int64_t step, int elem_bytes,
-                                  const void* send, void* dst, const int64_t* sbase, cudaStream_t st)
+                                  const void* send, void* dst, const int64_t* sbase, cudaStream_t st,
+                                  const Bounds& b)
 {
     const dim3 grid = step_grid(pairs_per_step(sched, t.src.P, B));
     if (elem_bytes == 16)
-        segment_unpack_kernel<uint4><<<grid, 128, 0, st>>>(t, sched, B, step, (const uint4*)send, (uint4*)dst, sbase);
+        segment_unpack_kernel<uint4><<<grid, 128, 0, st>>>(t, sched, B, step, (const uint4*)send, (uint4*)dst, sbase, b);
     else
-        segment_unpack_kernel<uint2><<<grid, 128, 0, st>>>(t, sched, B, step, (const uint2*)send, (uint2*)dst, sbase);
+        segment_unpack_kernel<uint2><<<grid, 128, 0, st>>>(t, sched, B, step, (const uint2*)send, (uint2*)dst, sbase, b);
     return cudaGetLastError();
 }
 
@@ -202,37 +209,38 @@ static unsigned grid_for(int64_t N, int sms)
 }
 
 cudaError_t launch_pack(const Transpose& t, int elem_bytes, const void* src, void* send,
-                        const int64_t* sbase, int64_t N, int sms, cudaStream_t st)
+                        const int64_t* sbase, int64_t N, int sms, cudaStream_t st, const Bounds& b)
 {
     if (N == 0) return cudaSuccess;
     if (elem_bytes == 16)
-        pack_kernel<uint4><<<grid_for(N, sms), 256, 0, st>>>(t, (const uint4*)src, (uint4*)send, sbase, N);
+        pack_kernel<uint4><<<grid_for(N, sms), 256, 0, st>>>(t, (const uint4*)src, (uint4*)send, sbase, N, b);
     else
-        pack_kernel<uint2><<<grid_for(N, sms), 256, 0, st>>>(t, (const uint2*)src, (uint2*)send, sbase, N);
+        pack_kernel<uint2><<<grid_for(N, sms), 256, 0, st>>>(t, (const uint2*)src, (uint2*)send, sbase, N, b);
     return cudaGetLastError();
 }
 
 cudaError_t launch_exchange(int elem_bytes, const int64_t* chunks, int64_t nchunks,
-                            const void* send, void* recv, int sms, cudaStream_t st)
+                            const void* send, void* recv, int sms, cudaStream_t st, const Bounds& b)
 {
     if (nchunks == 0) return cudaSuccess;
     int64_t cap = (int64_t)sms * 16;
     unsigned grid = (unsigned)(nchunks < cap ? nchunks : cap);
     if (elem_bytes == 16)
-        exchange_kernel<uint4><<<grid, 256, 0, st>>>(chunks, nchunks, (const uint4*)send, (uint4*)recv);
+        exchange_kernel<uint4><<<grid, 256, 0, st>>>(chunks, nchunks, (const uint4*)send, (uint4*)recv, b);
     else
-        exchange_kernel<uint2><<<grid, 256, 0, st>>>(chunks, nchunks, (const uint2*)send, (uint2*)recv);
+        exchange_kernel<uint2><<<grid, 256, 0, st>>>(chunks, nchunks, (const uint2*)send, (uint2*)recv, b);
     return cudaGetLastError();
 }
 
 cudaError_t launch_unpack(const Transpose& t, int elem_bytes, const void* buf, void* dst,
-                          const int64_t* base, int from_send, int64_t N, int sms, cudaStream_t st)
+                          const int64_t* base, int from_send, int64_t N, int sms, cudaStream_t st,
+                          const Bounds& b)
 {
     if (N == 0) return cudaSuccess;
     if (elem_bytes == 16)
-        unpack_kernel<uint4><<<grid_for(N, sms), 256, 0, st>>>(t, (const uint4*)buf, (uint4*)dst, base, from_send, N);
+        unpack_kernel<uint4><<<grid_for(N, sms), 256, 0, st>>>(t, (const uint4*)buf, (uint4*)dst, base, from_send, N, b);
     else
-        unpack_kernel<uint2><<<grid_for(N, sms), 256, 0, st>>>(t, (const uint2*)buf, (uint2*)dst, base, from_send, N);
+        unpack_kernel<uint2><<<grid_for(N, sms), 256, 0, st>>>(t, (const uint2*)buf, (uint2*)dst, base, from_send, N, b);
     return cudaGetLastError();
 }
 

@@ -4,6 +4,7 @@
 #include <stdint.h>
 #include <vector>
 #include "decomp.h"
+#include "checked.h"
 
 namespace ofg {
 
@@ -21,15 +22,15 @@ int64_t num_steps(int sched, int64_t P, int64_t B);
 int64_t pairs_per_step(int sched, int64_t P, int64_t B);
 cudaError_t launch_segment_exchange(int sched, int64_t P, int64_t B, int64_t step, int elem_bytes,
                                     const int64_t* C, const int64_t* sdispl, const int64_t* rdispl,
-                                    const void* send, void* recv, cudaStream_t st);
+                                    const void* send, void* recv, cudaStream_t st, const Bounds& b = Bounds());
 cudaError_t launch_segment_unpack(const Transpose& t, int sched, int64_t B, int64_t step, int elem_bytes,
-                                  const void* send, void* dst, const int64_t* sbase, cudaStream_t st);
+                                  const void* send, void* dst, const int64_t* sbase, cudaStream_t st, const Bounds& b = Bounds());
 
 cudaError_t launch_pack(const Transpose& t, int elem_bytes, const void* src, void* send,
-                        const int64_t* sbase, int64_t N, int sms, cudaStream_t st);
+                        const int64_t* sbase, int64_t N, int sms, cudaStream_t st, const Bounds& b = Bounds());
 cudaError_t launch_exchange(int elem_bytes, const int64_t* chunks, int64_t nchunks,
-                            const void* send, void* recv, int sms, cudaStream_t st);
+                            const void* send, void* recv, int sms, cudaStream_t st, const Bounds& b = Bounds());
 cudaError_t launch_unpack(const Transpose& t, int elem_bytes, const void* buf, void* dst,
-                          const int64_t* base, int from_send, int64_t N, int sms, cudaStream_t st);
+                          const int64_t* base, int from_send, int64_t N, int sms, cudaStream_t st, const Bounds& b = Bounds());
 
 }  // namespace ofg

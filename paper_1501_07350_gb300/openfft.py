@@ -18,7 +18,7 @@ from . import _build
 
 OK = 0
 ERR_INVALID_ARG, ERR_P_TOO_LARGE, ERR_UNSUPPORTED_RADIX, ERR_CUDA, ERR_NOMEM = 1, 2, 3, 4, 5
-ERR_TIMEOUT, ERR_ALIAS, ERR_UNSUPPORTED = 6, 7, 8
+ERR_TIMEOUT, ERR_ALIAS, ERR_UNSUPPORTED, ERR_BOUNDS = 6, 7, 8, 9
 
 C2C_F64, C2C_F32, C2C_SPLIT_BF16, C2C_SPLIT_TF32 = 0, 1, 2, 3
 R2C_F64, R2C_F32 = 4, 5
@@ -45,7 +45,7 @@ EXPORTS = [
     "openfft_num_features", "openfft_candidate_features", "openfft_tune_times", "openfft_set_cost_model",
     "openfft_tc_gemm", "openfft_exec_r2c", "openfft_exec_c2r", "openfft_tc_debug", "openfft_set_host_chunks",
     "openfft_exec_c2c_host_async", "openfft_set_copy_streams",
-    "openfft_debug_alloc_fail", "openfft_nd_plan", "openfft_nd_exec", "openfft_nd_destroy", "openfft_nd_set_stream",
+    "openfft_debug_alloc_fail", "openfft_checked_build", "openfft_debug_bounds_status", "openfft_nd_plan", "openfft_nd_exec", "openfft_nd_destroy", "openfft_nd_set_stream",
     "openfft_nd_box", "openfft_nd_decomp_box", "openfft_nd_decomp_counts", "openfft_dist_rows", "openfft_dist_counts", "openfft_dist_pack_host", "openfft_dist_unpack_host",
     "openfft_dist_plan", "openfft_dist_destroy", "openfft_dist_set_stream", "openfft_dist_elem_bytes",
     "openfft_dist_exchange_counts", "openfft_dist_stage", "openfft_dist_pack", "openfft_dist_unpack",
@@ -61,8 +61,14 @@ class OpenFFTError(RuntimeError):
         self.status = status
 
 
+def checked() -> bool:
+    """OPENFFT_GB_CHECKED=1 in the environment selects the bounds-checked
+    library (libopenfft_gb_checked.so, built by _build.build(checked=True))."""
+    return os.environ.get("OPENFFT_GB_CHECKED", "") == "1"
+
+
 def library_path() -> str:
-    return _build.LIB_PATH
+    return _build.CHECKED_LIB_PATH if checked() else _build.LIB_PATH
 
 
 def load():
@@ -71,7 +77,7 @@ def load():
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.LIB_PATH
+        path = library_path()
         if not os.path.exists(path):
             raise RuntimeError("libopenfft_gb.so is not built (%s); run `python -c \"import "
                                "__graft_entry__ as g; g.build()\"`" % path)
@@ -121,6 +127,8 @@ def load():
             "openfft_set_cost_model": (i32, [i32, i32, i32, pf]),
             "openfft_tc_gemm": (i32, [i32, i32, i32, i32, i32, pf, pf, pf]),
             "openfft_debug_alloc_fail": (i32, [ctypes.c_longlong]),
+            "openfft_checked_build": (i32, []),
+            "openfft_debug_bounds_status": (i32, [pi32]),
             "openfft_nd_plan": (vp, [i32, pi32, i32, i32]),
             "openfft_nd_exec": (i32, [vp, vp, vp, i32]),
             "openfft_nd_destroy": (None, [vp]),
@@ -308,6 +316,19 @@ def openfft_exec_c2c_noalloc(Na: int, Nb: int, Nc: int, P: int, dtype: int, inp,
 def openfft_debug_alloc_fail(nth: int) -> None:
     """Test control: the nth device allocation from now on fails (0 = off)."""
     _check(load().openfft_debug_alloc_fail(nth))
+
+
+def openfft_checked_build() -> bool:
+    """True when the loaded library is the bounds-checked build."""
+    return bool(load().openfft_checked_build())
+
+
+def openfft_debug_bounds_status() -> int:
+    """Checked build: the per-device bounds status word (0 or OPENFFT_ERR_BOUNDS),
+    read after synchronising the device, then cleared."""
+    st = ctypes.c_int(0)
+    _check(load().openfft_debug_bounds_status(ctypes.byref(st)))
+    return st.value
 
 
 # ------------------------------------------------- 4-D and 5-D transforms --

@@ -27,3 +27,18 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(autouse=True)
+def _bounds_status_of_the_checked_build():
+    """Under OPENFFT_GB_CHECKED=1 (the bounds-checked library), every test
+    also requires that no kernel met an index outside its array: the per-plan
+    words are reported by openfft_sync, the per-device word is read here."""
+    yield
+    if os.environ.get("OPENFFT_GB_CHECKED", "") != "1":
+        return
+    from paper_1501_07350_gb300 import openfft as of
+    if of._lib is None:
+        return
+    assert of.openfft_checked_build(), "OPENFFT_GB_CHECKED=1 but the normal library is loaded"
+    assert of.openfft_debug_bounds_status() == 0, "a kernel met a global index outside its array"

@@ -47,6 +47,22 @@ def test_every_declared_symbol_is_exported():
     assert declared == set(of.EXPORTS)
 
 
+def test_checked_build_compiles_and_exports_the_same_abi():
+    """The bounds-checked library (-DOPENFFT_CHECKED) builds for sm_103a,
+    exports every declared function and says which build it is; the normal
+    one refuses the bounds-status query.  Neither call touches a GPU."""
+    from paper_1501_07350_gb300 import _build
+    path = _build.build(checked=True)
+    chk = ctypes.CDLL(path)
+    for name in sorted(_declared_functions()):
+        assert hasattr(chk, name), name
+    assert chk.openfft_checked_build() == 1
+    assert not of.openfft_checked_build()
+    with pytest.raises(of.OpenFFTError) as e:
+        of.openfft_debug_bounds_status()
+    assert e.value.status == of.ERR_UNSUPPORTED
+
+
 ORDER_DIMS = {of.LAYOUT_ABC: lambda a, b, c: (a, b, c), of.LAYOUT_CAB: lambda a, b, c: (c, a, b),
               of.LAYOUT_CBA: lambda a, b, c: (c, b, a)}
 
