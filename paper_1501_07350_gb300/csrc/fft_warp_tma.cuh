@@ -74,9 +74,14 @@ struct TmaLine {
     using W = ArDP::W;
     static constexpr int kPasses = wplan_len(N);
     static constexpr int LS = warp_line_stride<16>(N);
+    static_assert(kPasses >= 2, "the entry fix-up rides on an in-place first pass");
 
-    // butterflies of pass P taken by part w of the line's threads
-    template <int P>
+    // butterflies of pass P taken by part w of the line's threads.  FIX (first
+    // pass only) is the entry fix-up of the stage's input, applied to each
+    // value as the butterfly reads it: bit 1, the shared-memory line holds
+    // complex128 (converted to double-float here); bit 0, conjugate (backward
+    // transform).  Reading and fixing in one step saves a pass over the line.
+    template <int P, int FIX = 0>
     __device__ __forceinline__ static void butterflies(const C* line, const W* __restrict__ tw, int lane, int w,
                                                        C (*v)[8], bool* ok)
     {
@@ -91,7 +96,14 @@ struct TmaLine {
             ok[u] = NBF % (32 * WPL) == 0 || b < NBF;
             if (ok[u]) {
 #pragma unroll
-                for (int j = 0; j < R; ++j) v[u][j] = line[wpad<16>(b + j * NBF)];
+                for (int j = 0; j < R; ++j) {
+                    C x = line[wpad<16>(b + j * NBF)];
+                    if constexpr ((FIX & 2) != 0)
+                        x = Io<ArDP>::from_c128(make_double2(__longlong_as_double((long long)x.x),
+                                                             __longlong_as_double((long long)x.y)));
+                    if constexpr ((FIX & 1) != 0) x = A::conj(x);
+                    v[u][j] = x;
+                }
                 if (m > 1) {
                     const int k = b % m;
 #pragma unroll
@@ -104,7 +116,7 @@ struct TmaLine {
     }
 
     // an in-place pass (all but the last)
-    template <int P>
+    template <int P, int FIX = 0>
     __device__ __forceinline__ static void pass(C* line, const W* __restrict__ tw, int lane, int w, int g)
     {
         constexpr int R = wplan_radix(N, P);
@@ -113,7 +125,7 @@ struct TmaLine {
         constexpr int NB = (NBF + 32 * WPL - 1) / (32 * WPL);
         C v[NB][8];
         bool ok[NB];
-        butterflies<P>(line, tw, lane, w, v, ok);
+        butterflies<P, FIX>(line, tw, lane, w, v, ok);
         line_sync<WPL>(g);
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
@@ -127,12 +139,12 @@ struct TmaLine {
         line_sync<WPL>(g);
     }
 
-    template <int P>
+    template <int P, int FIX = 0>
     __device__ __forceinline__ static void passes(C* line, const W* __restrict__ tw, int lane, int w, int g)
     {
         if constexpr (P < kPasses - 1) {
-            pass<P>(line, tw, lane, w, g);
-            passes<P + 1>(line, tw, lane, w, g);
+            pass<P, FIX>(line, tw, lane, w, g);
+            passes<P + 1, 0>(line, tw, lane, w, g);
         }
     }
 
@@ -208,20 +220,6 @@ __device__ __forceinline__ void tma_issue_load(const StageArgs& p, const TileGeo
     cp_async_commit();
 }
 
-template <int N, int WPL, bool CONVERT, bool CONJ>
-__device__ __forceinline__ void tma_fix(ArDP::C* line, int lane, int w)
-{
-#pragma unroll
-    for (int u = 0; u < N / (32 * WPL); ++u) {
-        ArDP::C* x = line + wpad<16>(lane + 32 * (w + WPL * u));
-        ArDP::C v;
-        if constexpr (CONVERT) v = Io<ArDP>::from_c128(*reinterpret_cast<const double2*>(x));
-        else v = *x;
-        if constexpr (CONJ) v = ArDP::conj(v);
-        *x = v;
-    }
-}
-
 // whether a line length runs with one input buffer and the staging area on it
 template <int N>
 constexpr bool tma_aliased() { return N >= 512; }
@@ -270,14 +268,19 @@ fft_warp_tma_kernel(const StageArgs p, int64_t ntiles, const __grid_constant__ C
             tma_issue_load<N, WPL>(p, tg, g, line, lane, w);
         }
         cp_async_wait_all();
-        if (convert) { if (p.conj_in) tma_fix<N, WPL, true, true>(line, lane, w); else tma_fix<N, WPL, true, false>(line, lane, w); }
-        else if (p.conj_in) tma_fix<N, WPL, false, true>(line, lane, w);
         line_sync<WPL>(g);
         if (!ALIASED) {
             const int64_t next = tile + gridDim.x;
             if (next < ntiles) tma_issue_load<N, WPL>(p, tile_geom(p, next, G), g, nxt + g * LS, lane, w);
         }
-        L::template passes<0>(line, tw, lane, w, g);
+        if (convert) {
+            if (p.conj_in) L::template passes<0, 3>(line, tw, lane, w, g);
+            else L::template passes<0, 2>(line, tw, lane, w, g);
+        } else if (p.conj_in) {
+            L::template passes<0, 1>(line, tw, lane, w, g);
+        } else {
+            L::template passes<0, 0>(line, tw, lane, w, g);
+        }
         if (!ALIASED) {
             if (tid == 0) bulk_wait_read_all();      // the previous tile's store has read the staging area
             __syncthreads();
