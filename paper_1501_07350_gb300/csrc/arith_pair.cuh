@@ -80,6 +80,7 @@ __device__ __forceinline__ u64 p2_splat(float x) { return p2_pack(x, x); }
 constexpr u64 kSgnPM = 0xBF8000003F800000ull;   // (+1, -1)
 constexpr u64 kSgnMP = 0x3F800000BF800000ull;   // (-1, +1)
 constexpr u64 kSignHi = 0x8000000000000000ull;  // sign bit of the high lane
+constexpr u64 kSignLo = 0x0000000080000000ull;  // sign bit of the low lane
 constexpr u64 kSignBoth = 0x8000000080000000ull;  // sign bits of both lanes
 
 struct ArDP {
@@ -92,9 +93,12 @@ struct ArDP {
     static constexpr int kElemBytes = 16;
 
     // The FMT_DF twiddle table of a power-of-two length n <= 512 holds n
-    // float4 entries (ArDF) followed by three arrays of n 16-byte slots: the
-    // components a, b and c of the per-pass tables of the warp kernel's radix
-    // plan (warp_plan.h).  table() points at array a.
+    // float4 entries (ArDF) followed by the per-pass table of the warp
+    // kernel's radix plan (warp_plan.h): entry e = off_p + (j - 1) m + k is
+    // the float4 (x, y, z, w) of W_n^(j k s_p), so a warp's lanes read
+    // consecutive entries.  table() points at the per-pass table.  The lane
+    // pairs of W are built from the entry with sign-bit operations (integer
+    // pipe): one 16-byte load per twiddle instead of three.
     __device__ __forceinline__ static const W* table(const void* tw, int n)
     {
         return reinterpret_cast<const W*>(reinterpret_cast<const char*>(tw) + 16 * (size_t)n);
@@ -102,12 +106,16 @@ struct ArDP {
     template <int N>
     __device__ __forceinline__ static W warp_twiddle(const W* tw, int off, int m, int j, int k, int)
     {
-        const ulonglong2* a = reinterpret_cast<const ulonglong2*>(tw);
         const int e = off + (j - 1) * m + k;
+        const float4 q = __ldg(reinterpret_cast<const float4*>(tw) + e);
+        const u64 xx = p2_splat(q.x), yy = p2_splat(q.y), zz = p2_splat(q.z), ww = p2_splat(q.w);
         W w;
-        w.a = __ldg(a + e);
-        w.b = __ldg(a + N + e);
-        w.c = __ldg(a + 2 * N + e);
+        w.a.x = xx;
+        w.a.y = xx ^ kSignBoth;            // (-x, -x)
+        w.b.x = yy ^ kSignLo;              // (-y, y)
+        w.b.y = yy ^ kSignHi;              // (y, -y)
+        w.c.x = zz;
+        w.c.y = ww ^ kSignLo;              // (-w, w)
         return w;
     }
 

@@ -48,7 +48,7 @@ fft_stage_kernel(const StageArgs p)
 
 // W[e] = exp(-2 pi i e / n), from the FP64 sincospi of 2e/n.  A double-float
 // table (FMT_DF) holds n float4 entries (hi and lo parts), followed by the
-// per-pass tables of the packed product (warp_twiddle_kernel): 64 n bytes.
+// per-pass table of the packed product (warp_twiddle_kernel): 32 n bytes.
 __global__ void twiddle_kernel(int n, int fmt, void* out)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -69,8 +69,8 @@ __global__ void twiddle_kernel(int n, int fmt, void* out)
 
 // The per-pass twiddle tables of the warp kernel's radix plan for the packed
 // double-float product (arith_pair.cuh, warp_plan.h): entry e of pass p is
-// W_n^(j k s_p), stored as three 16-byte components in arrays of n slots
-// after the n float4 entries of the FMT_DF table.
+// W_n^(j k s_p), stored as the float4 (hi re, hi im, lo re, lo im) in a
+// second array of n slots after the n float4 entries of the FMT_DF table.
 __global__ void warp_twiddle_kernel(int n, void* out)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -87,9 +87,7 @@ __global__ void warp_twiddle_kernel(int n, void* out)
     const float hr = (float)re, hi = (float)im;
     const float lr = (float)(re - (double)hr), li = (float)(im - (double)hi);
     float4* a = reinterpret_cast<float4*>(reinterpret_cast<char*>(out) + 16 * (size_t)n);
-    a[e] = make_float4(hr, hr, -hr, -hr);              // t0, -t0
-    a[n + e] = make_float4(-hi, hi, hi, -hi);          // t1 = (-im, im), -t1
-    a[2 * n + e] = make_float4(lr, lr, -li, li);       // t2 = (lo re, lo re), t3 = (-lo im, lo im)
+    a[e] = make_float4(hr, hi, lr, li);
 }
 
 // --------------------------------------------------------- host side ----

@@ -93,7 +93,7 @@ cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st);
 // Twiddle table of length n in format fmt (FMT_C128, FMT_C64 or FMT_DF);
 // twiddle_bytes(n, fmt) bytes at out.
 cudaError_t launch_twiddles(int n, int fmt, void* out, cudaStream_t st);
-inline size_t twiddle_bytes(int n, int fmt) { return (size_t)n * (fmt == FMT_C64 ? 8 : (fmt == FMT_DF ? 64 : 16)); }
+inline size_t twiddle_bytes(int n, int fmt) { return (size_t)n * (fmt == FMT_C64 ? 8 : (fmt == FMT_DF ? 32 : 16)); }
 
 // DFT-GEMM stages (dftgemm.cu): n = R S with 2 <= R, S <= 32 (radix[0] = R,
 // radix[1] = S); status receives OPENFFT_ERR_TIMEOUT if an MMA wait runs out.

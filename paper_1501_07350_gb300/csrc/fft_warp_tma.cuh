@@ -16,16 +16,14 @@
 // tensor map views the output as (grouped line coordinate, frequency, other
 // line coordinate) with element strides (1, Sk, So).
 //
-// Two tile layouts:
-//   * 256-point lines (DB): two input buffers and a separate staging area;
-//     the next tile's lines are copied (cp.async) while the current tile is
-//     transformed, and the staging area is reused one tile later, after the
-//     copy engine has read it.
-//   * 512-point lines (aliased): one input buffer, which the staging area
-//     overlays once every line's last-pass inputs are in registers; the next
-//     tile's copies start when the copy engine has read the staging area.
-//     Shared memory per CTA is that of the synchronous kernel, so as many
-//     CTAs stay resident; their loads and computations overlap.
+// Tile layout: the tile's lines, which the staging area overlays once every
+// line's last-pass inputs are in registers (a CTA barrier); the next tile's
+// copies (cp.async) start when the copy engine has read the staging area.
+// The lines are the CTA's only shared memory (19 KB for 4 lines of 256
+// points, 38 KB for 4 of 512), so many CTAs stay resident (8 and 4 per SM,
+// 32 warps) and one CTA's loads overlap the others' passes.  Measured on
+// 256^3 this beat two input buffers with a separate staging area (4 CTAs per
+// SM) by 6 %; on 512^3 double buffering with 3 CTAs per SM was 9 % slower.
 #pragma once
 #include <cuda.h>
 
@@ -71,8 +69,10 @@ __device__ __forceinline__ void line_sync(int g)
 // butterflies per pass, and a second warp would idle in those passes.
 template <int N, int G>
 constexpr int tma_wpl() { return N == 512 && G == 4 ? 2 : 1; }
-template <int G>
-constexpr int tma_min_ctas() { return G == 8 ? 2 : 4; }
+// CTAs per SM the register allocation is sized for: 64 registers a thread,
+// except 8-line CTAs of one warp per line (128)
+template <int N, int G>
+constexpr int tma_min_ctas() { return G == 8 ? 2 : (N == 256 ? 8 : 4); }
 
 // byte offset of output element (frequency k, tile line g) in the transposed
 // staging area: the tensor store's swizzle for rows of G x 16 bytes
@@ -184,10 +184,10 @@ struct TmaLine {
     }
 
     // the last pass, into the staging area: [k][G lines] swizzled rows
-    // (transposed output) or [line][k] (contiguous output).  ALIASED: the
-    // staging area overlays the input buffer, so every line's inputs are read
-    // (CTA barrier) before any result is written.
-    template <int G, bool ALIASED, bool CONTIG, bool CONJ_SCALE, bool EXT>
+    // (transposed output) or [line][k] (contiguous output).  The staging area
+    // overlays the tile's lines, so every line's inputs are read (CTA
+    // barrier) before any result is written.
+    template <int G, bool CONTIG, bool CONJ_SCALE, bool EXT>
     __device__ __forceinline__ static void last_pass(const C* line, const W* __restrict__ tw, unsigned char* stage,
                                                      int lane, int w, int g, double scale)
     {
@@ -199,7 +199,7 @@ struct TmaLine {
         C v[NB][8];
         bool ok[NB];
         butterflies<P>(line, tw, lane, w, v, ok);
-        if constexpr (ALIASED) __syncthreads();
+        __syncthreads();
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
             if (ok[u]) {
@@ -236,59 +236,40 @@ __device__ __forceinline__ void tma_issue_load(const StageArgs& p, const TileGeo
     cp_async_commit();
 }
 
-// whether a line length runs with one input buffer and the staging area on it
-template <int N>
-constexpr bool tma_aliased() { return N >= 512; }
-
 template <int N, int G>
 constexpr size_t tma_stage_bytes() { return (size_t)N * G * 16; }
+// 1024-byte alignment slack (the 128-byte swizzle), then the tile's lines,
+// which the staging area overlays
 template <int N, int G>
-constexpr size_t tma_smem_bytes()
-{
-    // 1024-byte alignment slack, then the staging area and two input buffers,
-    // or the one input buffer the staging area overlays
-    return tma_aliased<N>() ? 1024 + (size_t)G * warp_line_stride<16>(N) * 16
-                            : 1024 + tma_stage_bytes<N, G>() + 2 * (size_t)G * warp_line_stride<16>(N) * 16;
-}
+constexpr size_t tma_smem_bytes() { return 1024 + (size_t)G * warp_line_stride<16>(N) * 16; }
 
 template <int N, int G, bool CONTIG, bool CONJ_SCALE, bool EXT>
-__global__ void __launch_bounds__(32 * G * tma_wpl<N, G>(), tma_min_ctas<G>())
+__global__ void __launch_bounds__(32 * G * tma_wpl<N, G>(), tma_min_ctas<N, G>())
 fft_warp_tma_kernel(const StageArgs p, int64_t ntiles, const __grid_constant__ CUtensorMap tmap)
 {
     constexpr int WPL = tma_wpl<N, G>();
-    constexpr bool ALIASED = tma_aliased<N>();
     using L = TmaLine<N, WPL>;
     using C = ArDP::C;
     constexpr int LS = L::LS;
-    static_assert(tma_stage_bytes<N, G>() <= (size_t)G * LS * 16 || !ALIASED, "staging must fit the buffer");
+    static_assert(tma_stage_bytes<N, G>() <= (size_t)G * LS * 16, "staging must fit the lines");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t base = smem_addr(smem_raw);
-    unsigned char* aligned = smem_raw + (((base + 1023u) & ~1023u) - base);
-    unsigned char* stage = aligned;
-    C* cur = reinterpret_cast<C*>(ALIASED ? aligned : aligned + tma_stage_bytes<N, G>());
-    C* nxt = ALIASED ? cur : cur + G * LS;
+    unsigned char* stage = smem_raw + (((base + 1023u) & ~1023u) - base);
+    C* const lines = reinterpret_cast<C*>(stage);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = warp / WPL, w = warp % WPL;
+    C* const line = lines + g * LS;
     const ArDP::W* tw = ArDP::table(p.tw, N);
     const bool convert = p.in_fmt == FMT_C128;
 
-    int64_t tile = blockIdx.x;
-    if (!ALIASED && tile < ntiles) tma_issue_load<N, WPL>(p, tile_geom(p, tile, G), g, cur + g * LS, lane, w);
-    for (; tile < ntiles; tile += gridDim.x) {
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const TileGeom tg = tile_geom(p, tile, G);
-        C* line = cur + g * LS;
-        if (ALIASED) {
-            // the previous tile's store has read the buffer: copy this tile in
-            if (tid == 0) bulk_wait_read_all();
-            __syncthreads();
-            tma_issue_load<N, WPL>(p, tg, g, line, lane, w);
-        }
+        // the previous tile's store has read the staging area: copy this tile in
+        if (tid == 0) bulk_wait_read_all();
+        __syncthreads();
+        tma_issue_load<N, WPL>(p, tg, g, line, lane, w);
         cp_async_wait_all();
         line_sync<WPL>(g);
-        if (!ALIASED) {
-            const int64_t next = tile + gridDim.x;
-            if (next < ntiles) tma_issue_load<N, WPL>(p, tile_geom(p, next, G), g, nxt + g * LS, lane, w);
-        }
         if (convert) {
             if (p.conj_in) L::template passes<0, 3>(line, tw, lane, w, g);
             else L::template passes<0, 2>(line, tw, lane, w, g);
@@ -297,11 +278,7 @@ fft_warp_tma_kernel(const StageArgs p, int64_t ntiles, const __grid_constant__ C
         } else {
             L::template passes<0, 0>(line, tw, lane, w, g);
         }
-        if (!ALIASED) {
-            if (tid == 0) bulk_wait_read_all();      // the previous tile's store has read the staging area
-            __syncthreads();
-        }
-        L::template last_pass<G, ALIASED, CONTIG, CONJ_SCALE, EXT>(line, tw, stage, lane, w, g, p.scale);
+        L::template last_pass<G, CONTIG, CONJ_SCALE, EXT>(line, tw, stage, lane, w, g, p.scale);
         fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) {
@@ -320,7 +297,6 @@ fft_warp_tma_kernel(const StageArgs p, int64_t ntiles, const __grid_constant__ C
             }
             bulk_commit();
         }
-        C* t = cur; cur = nxt; nxt = t;
     }
     cp_async_wait_all();
     if (tid == 0) bulk_wait_all();
