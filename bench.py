@@ -342,9 +342,11 @@ def run_ours(args, rank, world, local_rank):
     roofline = stage_roofline(of, torch, dev, n, chosen, phases, clocks)
 
     # end to end through the host-buffer C ABI (copies inside the timed region).
-    # The three forward transforms are enqueued with the asynchronous call and
-    # then synchronised, so one plan's host-to-device copy can run beside
-    # another's device-to-host copy; then the three backward transforms.
+    # The six transforms of a step are enqueued with the asynchronous call and
+    # synchronised at the end, so one transform's host-to-device copy runs
+    # beside another's device-to-host copy.  Each backward transform reads the
+    # host output of its plan's forward transform: the library orders calls on
+    # one plan (an upload waits for the plan's previous download).
     up, down = torch.cuda.Stream(), torch.cuda.Stream()
     for P in PS:                    # one upload and one download queue for the three plans
         of.openfft_set_copy_streams(plans[P], up, down)
@@ -357,8 +359,6 @@ def run_ours(args, rank, world, local_rank):
     def host_step():
         for P in PS:
             of.openfft_exec_c2c_host_async(plans[P], xh, yh[P], of.FORWARD)
-        for P in PS:
-            of.openfft_sync(plans[P])
         for P in PS:
             of.openfft_exec_c2c_host_async(plans[P], yh[P], zh[P], of.BACKWARD)
         for P in PS:
@@ -385,8 +385,10 @@ def run_ours(args, rank, world, local_rank):
     e2e = {"value": round(job_value(work_per_step, world, t_e2e["async"] * 1e3), 2), "unit": UNIT,
            "h2d_bytes_per_step": 2 * len(PS) * N * 16, "d2h_bytes_per_step": 2 * len(PS) * N * 16,
            "steps": e2e_steps,
-           "calls": "openfft_exec_c2c_host_async, three plans enqueued then synchronised, forward then backward; "
-                    "the plans share one upload and one download stream",
+           "calls": "openfft_exec_c2c_host_async: three forward and then three backward transforms "
+                    "(three plans) enqueued, then synchronised; each backward reads its plan's forward "
+                    "output in host memory, ordered by the library; the plans share one upload and one "
+                    "download stream",
            "one_call_at_a_time": round(job_value(work_per_step, world, t_e2e["sync"] * 1e3), 2),
            "round_trip_rel_l2": e2e_err}
     del y_host, z_host

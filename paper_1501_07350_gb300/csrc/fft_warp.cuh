@@ -44,22 +44,27 @@ struct WarpLine {
     static constexpr int EB = sizeof(C);
     static constexpr int LS = warp_line_stride<EB>(N);
 
-    // One radix pass over L lines at line0 + i LS (i < L): lane b of the warp
-    // takes butterfly b of every line, so the L lines share the twiddle loads
-    // and give each thread L independent butterflies.
-    template <int P, int L>
+    // One radix pass over the warp's Q L lines at line0 + l LS.  The lanes
+    // form Q groups of S = 32 / Q; lane bl of group q takes butterflies
+    // bl, bl + S, ... of lines q L + i (i < L), so the L lines share the
+    // twiddle loads and give each thread L independent butterflies, and lines
+    // with fewer than 32 butterflies per pass still occupy every lane.
+    template <int P, int L, int Q = 1>
     __device__ __forceinline__ static void pass(C* line0, const W* __restrict__ tw, int lane)
     {
         constexpr int R = wplan_radix(N, P);
         constexpr int m = wplan_m(N, P);
         constexpr int s = N / (m * R);
         constexpr int NBF = N / R;
-        constexpr int NB = (NBF + 31) / 32;
+        constexpr int S = 32 / Q;
+        constexpr int NB = (NBF + S - 1) / S;
+        const int bl = lane % S;
+        line0 += (lane / S) * L * LS;
         C v[L][NB][R];
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
-            const int b = lane + 32 * u;
-            if (NBF % 32 == 0 || b < NBF) {
+            const int b = bl + S * u;
+            if (NBF % S == 0 || b < NBF) {
 #pragma unroll
                 for (int i = 0; i < L; ++i)
 #pragma unroll
@@ -81,8 +86,8 @@ struct WarpLine {
         __syncwarp();
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
-            const int b = lane + 32 * u;
-            if (NBF % 32 == 0 || b < NBF) {
+            const int b = bl + S * u;
+            if (NBF % S == 0 || b < NBF) {
                 const int t = b / m, k = b % m;
                 const int base = t * m * R + k;
 #pragma unroll
@@ -94,12 +99,12 @@ struct WarpLine {
         __syncwarp();
     }
 
-    template <int P, int L = 1>
+    template <int P, int L = 1, int Q = 1>
     __device__ __forceinline__ static void passes(C* line0, const W* __restrict__ tw, int lane)
     {
         if constexpr (P < kPasses) {
-            pass<P, L>(line0, tw, lane);
-            passes<P + 1, L>(line0, tw, lane);
+            pass<P, L, Q>(line0, tw, lane);
+            passes<P + 1, L, Q>(line0, tw, lane);
         }
     }
 };
@@ -218,13 +223,25 @@ constexpr bool warp_double_buffer() { return !(N >= 512 && sizeof(typename A::C)
 template <class A, int N, int G>
 constexpr int warp_lines_per_warp() { return (sizeof(typename A::C) == 8 && G % 2 == 0) ? 2 : 1; }
 
+// Line groups per warp: a radix-8 pass over n < 256 points has n / 8 < 32
+// butterflies, so 256 / n lines share a warp (as many as the tile has room
+// for), one group of lanes per line.
 template <class A, int N, int G>
-__global__ void __launch_bounds__(32 * G / warp_lines_per_warp<A, N, G>(),
-                                  warp_min_blocks(32 * G / warp_lines_per_warp<A, N, G>(), sizeof(typename A::C)))
+constexpr int warp_line_groups()
+{
+    return N >= 256 ? 1 : (256 / N < G / warp_lines_per_warp<A, N, G>() ? 256 / N : G / warp_lines_per_warp<A, N, G>());
+}
+template <class A, int N, int G>
+constexpr int warp_threads() { return 32 * G / (warp_lines_per_warp<A, N, G>() * warp_line_groups<A, N, G>()); }
+
+template <class A, int N, int G>
+__global__ void __launch_bounds__(warp_threads<A, N, G>(), warp_min_blocks(warp_threads<A, N, G>(), sizeof(typename A::C)))
 fft_warp_kernel(const StageArgs p, int64_t ntiles)
 {
     using C = typename A::C;
-    constexpr int L = warp_lines_per_warp<A, N, G>();
+    constexpr int Q = warp_line_groups<A, N, G>();
+    constexpr int L1 = warp_lines_per_warp<A, N, G>();      // lines per lane group
+    constexpr int L = L1 * Q;                                // this warp's lines
     constexpr int LS = warp_line_stride<sizeof(C)>(N);
     constexpr bool DB = warp_double_buffer<A, N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -262,7 +279,7 @@ fft_warp_kernel(const StageArgs p, int64_t ntiles)
 #pragma unroll
             for (int i = 0; i < L; ++i) warp_issue_load<A, N>(p, tn, g0 + i, nxt + (g0 + i) * LS, lane);
         }
-        WarpLine<A, N>::template passes<0, L>(line0, tw, lane);
+        WarpLine<A, N>::template passes<0, L1, Q>(line0, tw, lane);
         __syncthreads();                   // every line of the tile is transformed
         warp_store_dispatch<A, N, G, L>(p, tg, cur, tid);
         __syncthreads();                   // cur becomes the next copy target
@@ -274,7 +291,7 @@ fft_warp_kernel(const StageArgs p, int64_t ntiles)
 template <class A, int N, int G>
 cudaError_t launch_warp_n(const StageLaunch& L, cudaStream_t st)
 {
-    constexpr int T = 32 * G / warp_lines_per_warp<A, N, G>();
+    constexpr int T = warp_threads<A, N, G>();
     const size_t smem = (warp_double_buffer<A, N>() ? 2 : 1) * (size_t)G * warp_line_stride<sizeof(typename A::C)>(N) *
                         sizeof(typename A::C);
     static int cached[kMaxDevices] = {};          // CTAs per SM on each device, 0 = not yet known

@@ -154,6 +154,19 @@ def test_async_host_exec_across_plans(torch, shared_copy_streams):
         for z, w in zip(zs, want_b):
             assert np.array_equal(_bits(z.numpy()), _bits(w))
             assert oracle.rel_l2(z.numpy(), x) < 1e-12
+        # the benchmark's step: every forward, then every backward (each reading
+        # its plan's forward output in host memory), one synchronisation at the end
+        for y, z in zip(ys, zs):
+            y.fill_(float("nan")); z.fill_(float("nan"))
+        for h, y in zip(plans, ys):
+            of.openfft_exec_c2c_host_async(h, hx.numpy(), y.numpy(), of.FORWARD)
+        for h, y, z in zip(plans, ys, zs):
+            of.openfft_exec_c2c_host_async(h, y.numpy(), z.numpy(), of.BACKWARD)
+        for h in plans:
+            of.openfft_sync(h)
+        for y, z, wf, wb in zip(ys, zs, want_f, want_b):
+            assert np.array_equal(_bits(y.numpy()), _bits(wf))
+            assert np.array_equal(_bits(z.numpy()), _bits(wb))
         # two calls on one plan: the second reads the first one's output
         h, a, b = plans[0], ys[0], zs[0]
         a.fill_(float("nan")); b.fill_(float("nan"))
