@@ -370,21 +370,29 @@ def run_ours(args, rank, world, local_rank):
             of.openfft_exec_c2c_host(plans[P], yh[P], zh[P], of.BACKWARD)
 
     import torch.distributed as dist
-    e2e_steps = max(1, min(args.steps, 3))
-    t_e2e = {}
+    # The host link and host memory are shared with the machine's other GPUs,
+    # whose traffic shows up as occasional steps 1.5-2x slower: each step is
+    # timed on its own and the median is reported, every step beside it.
+    e2e_steps = 5
+    t_e2e, t_e2e_steps = {}, {}
     for name, fn in (("sync", host_step_sync), ("async", host_step)):
         fn()
-        if world > 1:
-            dist.barrier()
-        t0 = time.perf_counter()
+        per = []
         for _ in range(e2e_steps):
+            if world > 1:
+                dist.barrier()
+            t0 = time.perf_counter()
             fn()
-        t_e2e[name] = reduce_max((time.perf_counter() - t0) / e2e_steps, world, dev)
+            per.append(reduce_max(time.perf_counter() - t0, world, dev))
+        t_e2e[name] = float(np.median(per))
+        t_e2e_steps[name] = [round(v * 1e3, 1) for v in per]
     zr = zh[PS[-1]]
     e2e_err = float(np.linalg.norm(zr - x_np) / np.linalg.norm(x_np))
     e2e = {"value": round(job_value(work_per_step, world, t_e2e["async"] * 1e3), 2), "unit": UNIT,
            "h2d_bytes_per_step": 2 * len(PS) * N * 16, "d2h_bytes_per_step": 2 * len(PS) * N * 16,
-           "steps": e2e_steps,
+           "steps": e2e_steps, "statistic": "median of the steps, each timed on its own",
+           "step_ms": t_e2e_steps["async"], "one_call_at_a_time_step_ms": t_e2e_steps["sync"],
+           "mean": round(job_value(work_per_step, world, float(np.mean(t_e2e_steps["async"]))), 2),
            "calls": "openfft_exec_c2c_host_async: three forward and then three backward transforms "
                     "(three plans) enqueued, then synchronised; each backward reads its plan's forward "
                     "output in host memory, ordered by the library; the plans share one upload and one "
