@@ -61,18 +61,18 @@ __device__ __forceinline__ void line_sync(int g)
     else asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(32 * WPL) : "memory");
 }
 
-// warps per line.  512-point lines in CTAs of 4 lines take two: each lane
-// then holds one radix-8 butterfly (8 values) instead of two, which halves
-// the registers a thread needs (64) and doubles the resident warps per SM
-// (32) for the same shared memory; measured 5 % faster on 512^3 than one warp
-// per line.  256-point lines keep one: their 4 x 8 x 8 plan has 32 radix-8
-// butterflies per pass, and a second warp would idle in those passes.
+// warps per line.  512-point lines take two: each lane then holds one
+// radix-8 butterfly (8 values) instead of two, which halves the registers a
+// thread needs (64) and doubles the resident warps per SM (32) for the same
+// shared memory; measured 5 % faster on 512^3 than one warp per line (4-line
+// CTAs), 4 % with 8-line CTAs.  256-point lines keep one: their 4 x 8 x 8 plan
+// has 32 radix-8 butterflies per pass, and a second warp would idle there.
 template <int N, int G>
-constexpr int tma_wpl() { return N == 512 && G == 4 ? 2 : 1; }
+constexpr int tma_wpl() { return N == 512 ? 2 : 1; }
 // CTAs per SM the register allocation is sized for: 64 registers a thread,
-// except 8-line CTAs of one warp per line (128)
+// 32 warps per SM
 template <int N, int G>
-constexpr int tma_min_ctas() { return G == 8 ? 2 : (N == 256 ? 8 : 4); }
+constexpr int tma_min_ctas() { return G == 8 ? (N == 512 ? 2 : 4) : (N == 256 ? 8 : 4); }
 
 // byte offset of output element (frequency k, tile line g) in the transposed
 // staging area: the tensor store's swizzle for rows of G x 16 bytes
@@ -183,10 +183,12 @@ struct TmaLine {
         }
     }
 
-    // the last pass, into the staging area: [k][G lines] swizzled rows
-    // (transposed output) or [line][k] (contiguous output).  The staging area
-    // overlays the tile's lines, so every line's inputs are read (CTA
-    // barrier) before any result is written.
+    // the last pass, into the staging area.  Transposed output: [k][G lines]
+    // swizzled rows over the tile's lines, so every line's inputs are read
+    // (CTA barrier) before any result is written.  Contiguous output: [k] at
+    // the start of the line's own buffer, after the line's warps have read it
+    // (line barrier); the line's leader then stores it with one bulk copy, so
+    // these stages never synchronise the CTA.
     template <int G, bool CONTIG, bool CONJ_SCALE, bool EXT>
     __device__ __forceinline__ static void last_pass(const C* line, const W* __restrict__ tw, unsigned char* stage,
                                                      int lane, int w, int g, double scale)
@@ -199,7 +201,8 @@ struct TmaLine {
         C v[NB][8];
         bool ok[NB];
         butterflies<P>(line, tw, lane, w, v, ok);
-        __syncthreads();
+        if constexpr (CONTIG) line_sync<WPL>(g);
+        else __syncthreads();
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
             if (ok[u]) {
@@ -208,7 +211,7 @@ struct TmaLine {
 #pragma unroll
                 for (int q = 0; q < R; ++q) {
                     const int k = base + m * q;
-                    const uint32_t off = CONTIG ? (uint32_t)(g * N + k) * 16u : staged_offset<G>(k, g);
+                    const uint32_t off = CONTIG ? (uint32_t)k * 16u : staged_offset<G>(k, g);
                     *reinterpret_cast<uint4*>(stage + off) = out16<CONJ_SCALE, EXT>(v[u][q], scale);
                 }
             }
@@ -265,8 +268,10 @@ fft_warp_tma_kernel(const StageArgs p, int64_t ntiles, const __grid_constant__ C
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const TileGeom tg = tile_geom(p, tile, G);
         // the previous tile's store has read the staging area: copy this tile in
-        if (tid == 0) bulk_wait_read_all();
-        __syncthreads();
+        const bool leader = CONTIG ? (w == 0 && lane == 0) : tid == 0;
+        if (leader) bulk_wait_read_all();
+        if constexpr (CONTIG) line_sync<WPL>(g);
+        else __syncthreads();
         tma_issue_load<N, WPL>(p, tg, g, line, lane, w);
         cp_async_wait_all();
         line_sync<WPL>(g);
@@ -278,8 +283,19 @@ fft_warp_tma_kernel(const StageArgs p, int64_t ntiles, const __grid_constant__ C
         } else {
             L::template passes<0, 0>(line, tw, lane, w, g);
         }
-        L::template last_pass<G, CONTIG, CONJ_SCALE, EXT>(line, tw, stage, lane, w, g, p.scale);
+        L::template last_pass<G, CONTIG, CONJ_SCALE, EXT>(line, tw, CONTIG ? reinterpret_cast<unsigned char*>(line) : stage,
+                                                         lane, w, g, p.scale);
         fence_proxy_async_smem();
+        if constexpr (CONTIG) {
+            line_sync<WPL>(g);
+            if (leader && g < tg.valid) {
+                const int64_t o = tg.obase + g * tg.ostride;
+                if (in_bounds(p.chk, o, p.out_elems) && in_bounds(p.chk, o + N - 1, p.out_elems))
+                    bulk_store(reinterpret_cast<char*>(p.out) + o * 16, smem_addr(line), N * 16u);
+                bulk_commit();
+            }
+            continue;
+        }
         __syncthreads();
         if (tid == 0) {
             if constexpr (!CONTIG) {
@@ -299,7 +315,7 @@ fft_warp_tma_kernel(const StageArgs p, int64_t ntiles, const __grid_constant__ C
         }
     }
     cp_async_wait_all();
-    if (tid == 0) bulk_wait_all();
+    if (CONTIG ? (tid % (32 * WPL)) == 0 : tid == 0) bulk_wait_all();
 }
 
 // host side ----------------------------------------------------------------
