@@ -49,8 +49,10 @@ struct WarpLine {
     // bl, bl + S, ... of lines q L + i (i < L), so the L lines share the
     // twiddle loads and give each thread L independent butterflies, and lines
     // with fewer than 32 butterflies per pass still occupy every lane.
-    template <int P, int L, int Q = 1>
-    __device__ __forceinline__ static void pass(C* line0, const W* __restrict__ tw, int lane)
+    // The pass's results go through put(l, k, value): value k of the warp's
+    // line l (l < Q L), after every lane has read its inputs.
+    template <int P, int L, int Q, class Put>
+    __device__ __forceinline__ static void pass_to(const C* line0, const W* __restrict__ tw, int lane, Put put)
     {
         constexpr int R = wplan_radix(N, P);
         constexpr int m = wplan_m(N, P);
@@ -59,7 +61,8 @@ struct WarpLine {
         constexpr int S = 32 / Q;
         constexpr int NB = (NBF + S - 1) / S;
         const int bl = lane % S;
-        line0 += (lane / S) * L * LS;
+        const int l0 = (lane / S) * L;
+        line0 += l0 * LS;
         C v[L][NB][R];
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
@@ -93,9 +96,15 @@ struct WarpLine {
 #pragma unroll
                 for (int i = 0; i < L; ++i)
 #pragma unroll
-                    for (int q = 0; q < R; ++q) line0[i * LS + wpad<EB>(base + m * q)] = v[i][u][q];
+                    for (int q = 0; q < R; ++q) put(l0 + i, base + m * q, v[i][u][q]);
             }
         }
+    }
+
+    template <int P, int L, int Q = 1>
+    __device__ __forceinline__ static void pass(C* line0, const W* __restrict__ tw, int lane)
+    {
+        pass_to<P, L, Q>(line0, tw, lane, [=](int l, int k, const C& x) { line0[l * LS + wpad<EB>(k)] = x; });
         __syncwarp();
     }
 
@@ -105,6 +114,16 @@ struct WarpLine {
         if constexpr (P < kPasses) {
             pass<P, L, Q>(line0, tw, lane);
             passes<P + 1, L, Q>(line0, tw, lane);
+        }
+    }
+
+    // every pass but the last, in place
+    template <int P, int L = 1, int Q = 1>
+    __device__ __forceinline__ static void passes_but_last(C* line0, const W* __restrict__ tw, int lane)
+    {
+        if constexpr (P < kPasses - 1) {
+            pass<P, L, Q>(line0, tw, lane);
+            passes_but_last<P + 1, L, Q>(line0, tw, lane);
         }
     }
 };
