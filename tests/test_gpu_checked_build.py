@@ -4,9 +4,9 @@ A child pytest process loads libopenfft_gb_checked.so (OPENFFT_GB_CHECKED=1)
 and runs the parity tests of every C2C form on small shapes: every candidate
 of 32^3 P = 4 and of the small mixed-radix shapes, the transposes of every
 exchange method, the longest axes, the 256- and 512-point axes of the
-power-of-two warp kernels and their asynchronous-output form, the host-buffer
-entry points (line-range launches), the D-dimensional plans and the
-multi-device steps on one device.  Each test there still compares with the
+power-of-two warp kernels and their asynchronous-output form (with ragged
+tiles), the host-buffer entry points (line-range launches), the D-dimensional
+plans and the multi-device steps on one device.  Each test there still compares with the
 oracle at its own bar, and additionally every kernel's global indices are
 checked: openfft_sync fails with OPENFFT_ERR_BOUNDS on a plan's word and the
 conftest fixture reads the per-device word after each test.  No test plants
@@ -27,7 +27,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 SELECTION = [
     ("tests/test_gpu_fft.py", "32cubed or small_shapes or transposes_bit_exact or longest_axes or mixed_radix"),
-    ("tests/test_gpu_parity_bench.py", "long_power_of_two_axes"),
+    ("tests/test_gpu_parity_bench.py", "long_power_of_two_axes or ragged_tiles"),
     ("tests/test_gpu_host_exec.py", ""),
     ("tests/test_gpu_nd.py", ""),
     ("tests/test_gpu_dist.py", ""),

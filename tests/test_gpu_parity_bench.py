@@ -98,6 +98,22 @@ def test_long_power_of_two_axes_every_candidate(torch, shape, P, dtype):
         of.openfft_destroy(plan)
 
 
+# Ragged tiles of the asynchronous-output kernels: the grouped line count is
+# not a multiple of the tile (4 / 8 lines complex128, 8 / 16 complex64), so
+# the last tile's tensor store is clipped at the output's edge, and the
+# per-line contiguous store leaves its missing lines out.  (6, 256, 7):
+# forward stage 2 grouped over 6 lines, backward stage 2 over 7;
+# (5, 6, 512): forward stage 1 over 30; (512, 5, 6): backward stage 1 over 5
+# and the contiguous forward stage 3.
+RAGGED_SHAPES = [((6, 256, 7), 6), ((5, 6, 512), 5), ((512, 5, 6), 3)]
+
+
+@pytest.mark.parametrize("dtype", [of.C2C_F64, of.C2C_F32])
+@pytest.mark.parametrize("shape,P", RAGGED_SHAPES)
+def test_async_output_ragged_tiles_every_candidate(torch, shape, P, dtype):
+    test_long_power_of_two_axes_every_candidate(torch, shape, P, dtype)
+
+
 # ------------------------------------------------------------- 256^3 ------
 
 def _x256():
