@@ -21,7 +21,7 @@ CHECKED_DIR = os.path.join(HERE, "_build_checked")
 CHECKED_LIB_PATH = os.path.join(CHECKED_DIR, "libopenfft_gb_checked.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["capi.cu", "fft_stage.cu", "redistribute.cu", "fft_tile_f64.cu", "fft_tile_df.cu", "fft_tile_f32.cu", "noalloc.cu", "batch.cu", "mlp.cu", "tcgemm.cu", "dftgemm.cu", "r2c.cu", "dist.cu", "fft_tma_256.cu", "fft_tma_512.cu", "nd.cu", "fft_tma_f32.cu"]
+SOURCES = ["capi.cu", "fft_stage.cu", "redistribute.cu", "fft_tile_f64.cu", "fft_tile_df.cu", "fft_tile_f32.cu", "noalloc.cu", "batch.cu", "mlp.cu", "tcgemm.cu", "dftgemm.cu", "r2c.cu", "dist.cu", "fft_tma_256.cu", "fft_tma_512.cu", "nd.cu", "fft_tma_f32.cu", "fft_warp_mixed.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + CSRC, "-I" + INCLUDE]

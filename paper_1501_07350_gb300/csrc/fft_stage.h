@@ -90,6 +90,8 @@ cudaError_t launch_tile_df(const StageLaunch& L, cudaStream_t st, bool* handled)
 cudaError_t launch_warp_tma_256(const StageLaunch& L, cudaStream_t st, bool* handled);
 cudaError_t launch_warp_tma_512(const StageLaunch& L, cudaStream_t st, bool* handled);
 cudaError_t launch_warp_tma_f32(const StageLaunch& L, cudaStream_t st, bool* handled);
+cudaError_t launch_warp_mixed_df(const StageLaunch& L, cudaStream_t st, bool* handled);
+cudaError_t launch_warp_mixed_f32(const StageLaunch& L, cudaStream_t st, bool* handled);
 cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st);
 // Twiddle table of length n in format fmt (FMT_C128, FMT_C64 or FMT_DF);
 // twiddle_bytes(n, fmt) bytes at out.

@@ -19,6 +19,10 @@ cudaError_t launch_tile_df(const StageLaunch& L, cudaStream_t st, bool* handled)
         cudaError_t e = L.args.G == 4 ? launch_warp_g<ArDP, 4>(L, st, handled) : launch_warp_g<ArDP, 8>(L, st, handled);
         if (*handled || e) return e;
     }
+    if ((L.family == KERNEL_AUTO || L.family == KERNEL_WARP) && warp_mixed_length(L.args.n)) {
+        cudaError_t e = launch_warp_mixed_df(L, st, handled);
+        if (*handled || e) return e;
+    }
     if (L.family == KERNEL_WARP) return cudaSuccess;
     if (L.args.G == 4) return launch_tile_g<ArDF, 4>(L, st, handled);
     if (L.args.G == 8) return launch_tile_g<ArDF, 8>(L, st, handled);

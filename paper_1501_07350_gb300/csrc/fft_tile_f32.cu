@@ -18,6 +18,10 @@ cudaError_t launch_tile_f32(const StageLaunch& L, cudaStream_t st, bool* handled
         cudaError_t e = L.args.G == 8 ? launch_warp_g<ArF32, 8>(L, st, handled) : launch_warp_g<ArF32, 16>(L, st, handled);
         if (*handled || e) return e;
     }
+    if ((L.family == KERNEL_AUTO || L.family == KERNEL_WARP) && warp_mixed_length(L.args.n)) {
+        cudaError_t e = launch_warp_mixed_f32(L, st, handled);
+        if (*handled || e) return e;
+    }
     if (L.family == KERNEL_WARP) return cudaSuccess;
     if (L.args.G == 8) return launch_tile_g<ArF32, 8>(L, st, handled);
     if (L.args.G == 16) return launch_tile_g<ArF32, 16>(L, st, handled);

@@ -137,14 +137,15 @@ __device__ __forceinline__ void warp_issue_load(const StageArgs& p, const TileGe
     if (g < tg.valid) {
         const char* src = reinterpret_cast<const char*>(p.in) + (tg.line0 + g * tg.lstride) * (int64_t)(N * EB);
 #pragma unroll
-        for (int u = 0; u < N / 32; ++u) {
+        for (int u = 0; u < (N + 31) / 32; ++u) {
             const int pos = lane + 32 * u;
-            if (in_bounds(p.chk, (tg.line0 + g * tg.lstride) * N + pos, p.in_elems))
+            if ((N % 32 == 0 || pos < N) && in_bounds(p.chk, (tg.line0 + g * tg.lstride) * N + pos, p.in_elems))
                 cp_async<EB>(line + wpad<sizeof(typename A::C)>(pos), src + pos * EB);
         }
     } else {
 #pragma unroll
-        for (int u = 0; u < N / 32; ++u) line[wpad<sizeof(typename A::C)>(lane + 32 * u)] = A::zero();
+        for (int u = 0; u < (N + 31) / 32; ++u)
+            if (N % 32 == 0 || lane + 32 * u < N) line[wpad<sizeof(typename A::C)>(lane + 32 * u)] = A::zero();
     }
     cp_async_commit();
 }
@@ -154,7 +155,8 @@ __device__ __forceinline__ void warp_fix(typename A::C* line, int lane)
 {
     using C = typename A::C;
 #pragma unroll
-    for (int u = 0; u < N / 32; ++u) {
+    for (int u = 0; u < (N + 31) / 32; ++u) {
+        if (N % 32 != 0 && lane + 32 * u >= N) break;
         C* x = line + wpad<sizeof(C)>(lane + 32 * u);
         C v;
         if constexpr (CONVERT) v = Io<A>::from_c128(*reinterpret_cast<const double2*>(x));
@@ -196,9 +198,9 @@ __device__ __forceinline__ void warp_tile_store(const StageArgs& p, const TileGe
             const typename A::C* line = buf + g * LS;
             char* ptr = first + (int64_t)g * tg.ostride * EB;
 #pragma unroll
-            for (int u = 0; u < N / 32; ++u) {
+            for (int u = 0; u < (N + 31) / 32; ++u) {
                 const int k = lane + 32 * u;
-                if (in_bounds(p.chk, tg.obase + (int64_t)g * tg.ostride + k, p.out_elems))
+                if ((N % 32 == 0 || k < N) && in_bounds(p.chk, tg.obase + (int64_t)g * tg.ostride + k, p.out_elems))
                     put<A, CONJ_SCALE, EXT>(ptr + k * EB, line[wpad<CB>(k)], p.scale);
             }
         }
@@ -243,12 +245,14 @@ template <class A, int N, int G>
 constexpr int warp_lines_per_warp() { return (sizeof(typename A::C) == 8 && G % 2 == 0) ? 2 : 1; }
 
 // Line groups per warp: a radix-8 pass over n < 256 points has n / 8 < 32
-// butterflies, so 256 / n lines share a warp (as many as the tile has room
-// for), one group of lanes per line.
+// butterflies, so up to 256 / n lines share a warp (a power of two, as many
+// as the tile has room for), one group of lanes per line.
 template <class A, int N, int G>
 constexpr int warp_line_groups()
 {
-    return N >= 256 ? 1 : (256 / N < G / warp_lines_per_warp<A, N, G>() ? 256 / N : G / warp_lines_per_warp<A, N, G>());
+    int q = 1;                                 // a power of two: 32 / q lanes per line
+    while (2 * q <= 256 / N && 2 * q <= G / warp_lines_per_warp<A, N, G>()) q *= 2;
+    return q;
 }
 template <class A, int N, int G>
 constexpr int warp_threads() { return 32 * G / (warp_lines_per_warp<A, N, G>() * warp_line_groups<A, N, G>()); }
