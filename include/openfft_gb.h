@@ -124,7 +124,8 @@ enum {
     OPENFFT_TUNE_DEFAULT = 0,    /* fixed default variant                         */
     OPENFFT_TUNE_EXHAUSTIVE = 1, /* time every candidate twice, keep the fastest   */
     OPENFFT_TUNE_LEARNED = 2,    /* the installed cost model's fastest candidate (no model: DEFAULT) */
-    OPENFFT_TUNE_USER = 3        /* candidate index given by the caller            */
+    OPENFFT_TUNE_USER = 3,       /* candidate index given by the caller            */
+    OPENFFT_TUNE_SAVED = 4       /* the recorded choice for this problem (openfft_tuning_*), else EXHAUSTIVE */
 };
 
 /* ------------------------------------------------------------ plans ---- */
@@ -246,12 +247,14 @@ int openfft_decomp_degree(int Na, int Nb, int Nc, int P, int layout);
 /* Choose how the plan is executed.  mode: OPENFFT_TUNE_*.  With USER,
  * `candidate` indexes the list of openfft_num_candidates (otherwise ignored).
  * EXHAUSTIVE runs every candidate twice on plan-owned buffers (the paper's
- * 2 runs per method) and keeps the fastest. */
+ * 2 runs per method) and keeps the fastest.  SAVED takes the choice recorded
+ * for this problem (see openfft_tuning_save below). */
 int openfft_set_tuning(openfft_plan_t plan, int mode, int candidate);
 
-/* Stage-kernel families: one warp per line (power-of-two lengths), tiles of
- * lines specialised per length, or the generic kernel (any length); AUTO
- * takes the first of these that exists for the length. */
+/* Stage-kernel families: one warp per line (power-of-two lengths 32..512 and
+ * the mixed-radix lengths 48..160), tiles of lines specialised per length, or
+ * the generic kernel (any length); AUTO takes the first of these that exists
+ * for the length. */
 enum { OPENFFT_KERNEL_AUTO = 0, OPENFFT_KERNEL_WARP = 1, OPENFFT_KERNEL_TILE = 2, OPENFFT_KERNEL_GENERIC = 3 };
 
 /* Number of execution candidates of this plan and a description of one
@@ -260,6 +263,29 @@ enum { OPENFFT_KERNEL_AUTO = 0, OPENFFT_KERNEL_WARP = 1, OPENFFT_KERNEL_TILE = 2
 int openfft_num_candidates(openfft_plan_t plan);
 int openfft_candidate(openfft_plan_t plan, int index, int* variant, int* arith,
                       int* lines_per_cta, int* kernel);
+
+/* Persisted tuning choices: the paper's "User-select" reuse of a method chosen
+ * by an earlier tuning run, so that the initialisation skips the timing runs
+ * (Sec. 3.2.3).  A process-wide table maps a problem (Na, Nb, Nc, P, dtype) to
+ * the candidate its tuning chose, described as openfft_candidate describes it
+ * (variant, arithmetic, lines per CTA, kernel family).  Every EXHAUSTIVE or
+ * LEARNED tuning records its choice; OPENFFT_TUNE_SAVED selects the recorded
+ * candidate, and runs (and records) EXHAUSTIVE when the problem has no entry or
+ * its entry describes no candidate of this plan.  Thread-safe.
+ *
+ * openfft_tuning_save writes the table to a text file, one problem per line:
+ * "Na Nb Nc P dtype variant arith lines_per_cta kernel" (lines starting with
+ * '#' are comments).  openfft_tuning_load merges such a file into the table
+ * (entries of the file replace those of the same problem); a malformed line
+ * (not nine integers, a size or P below 1, an unknown dtype) makes the call
+ * return OPENFFT_ERR_INVALID_ARG naming the line, with the table unchanged.
+ * openfft_tuning_lookup sets *found to 1 and choice[0..3] to the entry of a
+ * problem, or *found to 0.  openfft_tuning_clear empties the table.  None of
+ * these calls touches the GPU. */
+int openfft_tuning_save(const char* path);
+int openfft_tuning_load(const char* path);
+int openfft_tuning_lookup(int Na, int Nb, int Nc, int P, int dtype, int* found, int choice[4]);
+int openfft_tuning_clear(void);
 /* Index of the candidate exec currently uses. */
 int openfft_current_candidate(openfft_plan_t plan);
 

@@ -12,7 +12,9 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <array>
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -1202,11 +1204,136 @@ int openfft_candidate(openfft_plan_t plan, int index, int* variant, int* arith, 
 
 int openfft_current_candidate(openfft_plan_t plan) { return plan ? plan->current : -1; }
 
+}  // extern "C"
+
+// ------------------------------------------------ persisted tuning choices --
+// The candidate each tuned problem chose, described as openfft_candidate
+// describes it, per (Na, Nb, Nc, P, dtype): the paper's "User-select" reuse of
+// an earlier tuning (Sec. 3.2.3).  Process-wide; saved to and merged from
+// text files.
+namespace {
+
+using TunedKey = std::array<int, 5>;
+using TunedChoice = std::array<int, 4>;
+std::mutex g_tuned_mu;
+std::map<TunedKey, TunedChoice> g_tuned;
+
+TunedKey tuned_key(const openfft_plan_s* p) { return TunedKey{p->Na, p->Nb, p->Nc, p->P, p->dtype}; }
+
+TunedChoice describe_candidate(openfft_plan_s* p, int index)
+{
+    TunedChoice c{};
+    openfft_candidate(p, index, &c[0], &c[1], &c[2], &c[3]);
+    return c;
+}
+
+void record_choice(openfft_plan_s* p)
+{
+    const TunedChoice c = describe_candidate(p, p->current);
+    std::lock_guard<std::mutex> lk(g_tuned_mu);
+    g_tuned[tuned_key(p)] = c;
+}
+
+// index of the recorded candidate of p's problem, -1 if none
+int saved_candidate(openfft_plan_s* p)
+{
+    TunedChoice want;
+    {
+        std::lock_guard<std::mutex> lk(g_tuned_mu);
+        auto it = g_tuned.find(tuned_key(p));
+        if (it == g_tuned.end()) return -1;
+        want = it->second;
+    }
+    for (int i = 0; i < (int)p->cands.size(); ++i)
+        if (describe_candidate(p, i) == want) return i;
+    return -1;
+}
+
+bool valid_dtype(int dtype)
+{
+    return dtype == OPENFFT_C2C_F64 || dtype == OPENFFT_C2C_F32 || dtype == OPENFFT_C2C_SPLIT_BF16 ||
+           dtype == OPENFFT_C2C_SPLIT_TF32 || dtype == OPENFFT_R2C_F64 || dtype == OPENFFT_R2C_F32;
+}
+
+}  // namespace
+
+extern "C" {
+
+int openfft_tuning_save(const char* path)
+{
+    if (!path) return fail(OPENFFT_ERR_INVALID_ARG, "null path");
+    std::map<TunedKey, TunedChoice> copy;
+    {
+        std::lock_guard<std::mutex> lk(g_tuned_mu);
+        copy = g_tuned;
+    }
+    FILE* f = std::fopen(path, "w");
+    if (!f) return fail(OPENFFT_ERR_INVALID_ARG, (std::string("cannot write ") + path).c_str());
+    bool ok = std::fprintf(f, "# openfft tuning choices: Na Nb Nc P dtype variant arith lines_per_cta kernel\n") > 0;
+    for (const auto& e : copy)
+        ok = ok && std::fprintf(f, "%d %d %d %d %d %d %d %d %d\n", e.first[0], e.first[1], e.first[2], e.first[3],
+                                e.first[4], e.second[0], e.second[1], e.second[2], e.second[3]) > 0;
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? OPENFFT_OK : fail(OPENFFT_ERR_INVALID_ARG, (std::string("cannot write ") + path).c_str());
+}
+
+int openfft_tuning_load(const char* path)
+{
+    if (!path) return fail(OPENFFT_ERR_INVALID_ARG, "null path");
+    FILE* f = std::fopen(path, "r");
+    if (!f) return fail(OPENFFT_ERR_INVALID_ARG, (std::string("cannot read ") + path).c_str());
+    std::map<TunedKey, TunedChoice> add;
+    char line[512];
+    int lineno = 0;
+    while (std::fgets(line, sizeof line, f)) {
+        ++lineno;
+        const char* s = line;
+        while (*s == ' ' || *s == '\t') ++s;
+        if (*s == '#' || *s == '\n' || *s == '\r' || *s == '\0') continue;
+        int v[9], used = 0;
+        const int n = std::sscanf(s, "%d %d %d %d %d %d %d %d %d %n", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6],
+                                  &v[7], &v[8], &used);
+        const bool rest_empty = n == 9 && s[used] == '\0';
+        if (n != 9 || !rest_empty || v[0] < 1 || v[1] < 1 || v[2] < 1 || v[3] < 1 || !valid_dtype(v[4])) {
+            std::fclose(f);
+            return fail(OPENFFT_ERR_INVALID_ARG, (std::string(path) + ": malformed line " + std::to_string(lineno)).c_str());
+        }
+        add[TunedKey{v[0], v[1], v[2], v[3], v[4]}] = TunedChoice{v[5], v[6], v[7], v[8]};
+    }
+    std::fclose(f);
+    std::lock_guard<std::mutex> lk(g_tuned_mu);
+    for (const auto& e : add) g_tuned[e.first] = e.second;
+    return OPENFFT_OK;
+}
+
+int openfft_tuning_lookup(int Na, int Nb, int Nc, int P, int dtype, int* found, int choice[4])
+{
+    if (!found) return fail(OPENFFT_ERR_INVALID_ARG, "null output");
+    std::lock_guard<std::mutex> lk(g_tuned_mu);
+    auto it = g_tuned.find(TunedKey{Na, Nb, Nc, P, dtype});
+    *found = it != g_tuned.end();
+    if (*found && choice)
+        for (int i = 0; i < 4; ++i) choice[i] = it->second[(size_t)i];
+    return OPENFFT_OK;
+}
+
+int openfft_tuning_clear(void)
+{
+    std::lock_guard<std::mutex> lk(g_tuned_mu);
+    g_tuned.clear();
+    return OPENFFT_OK;
+}
+
 int openfft_set_tuning(openfft_plan_t plan, int mode, int candidate)
 {
     if (!plan) return fail(OPENFFT_ERR_INVALID_ARG, "null plan");
     if (plan->batch) return fail(OPENFFT_ERR_INVALID_ARG, "batched plans have a single execution path");
     switch (mode) {
+    case OPENFFT_TUNE_SAVED: {
+        const int idx = saved_candidate(plan);
+        if (idx >= 0 && select_candidate(plan, idx) == OPENFFT_OK) return OPENFFT_OK;
+        return openfft_set_tuning(plan, OPENFFT_TUNE_EXHAUSTIVE, 0);
+    }
     case OPENFFT_TUNE_DEFAULT:
         return select_candidate(plan, 0);
     case OPENFFT_TUNE_USER:
@@ -1219,7 +1346,9 @@ int openfft_set_tuning(openfft_plan_t plan, int mode, int candidate)
         for (int i = 0; i < (int)ms.size(); ++i)
             if (ms[(size_t)i] >= 0.f && (best < 0 || ms[(size_t)i] < ms[(size_t)best])) best = i;
         if (best < 0) return fail(OPENFFT_ERR_UNSUPPORTED, "no candidate ran");
-        return select_candidate(plan, best);
+        const int sel = select_candidate(plan, best);
+        if (!sel) record_choice(plan);
+        return sel;
     }
     case OPENFFT_TUNE_LEARNED: {
         std::vector<float> model;
@@ -1242,7 +1371,11 @@ int openfft_set_tuning(openfft_plan_t plan, int mode, int candidate)
         std::vector<int> order((size_t)nc);
         for (int i = 0; i < nc; ++i) order[(size_t)i] = i;
         std::sort(order.begin(), order.end(), [&](int a2, int b2) { return y[(size_t)a2] < y[(size_t)b2]; });
-        for (int i : order) if (!select_candidate(plan, i)) return OPENFFT_OK;
+        for (int i : order)
+            if (!select_candidate(plan, i)) {
+                record_choice(plan);
+                return OPENFFT_OK;
+            }
         return fail(OPENFFT_ERR_UNSUPPORTED, "no candidate can be built");
     }
     default:

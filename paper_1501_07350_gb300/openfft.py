@@ -29,7 +29,7 @@ VARIANT_ISEND_WAITALL, VARIANT_ISEND_WAITALL_BLOCK, VARIANT_ISEND_WAITSOME_BLOCK
 METHODS = {"Alltoallv": 0, "Isend_Waitsome": 1, "fused": 2, "Isend_Waitall": 3, "Isend_Waitall_Block": 4,
            "Isend_Waitsome_Block": 5, "Sendrecv": 6}
 ARITH_NATIVE, ARITH_DOUBLE_FLOAT, ARITH_TC_TF32, ARITH_TC_BF16 = 0, 1, 2, 3
-TUNE_DEFAULT, TUNE_EXHAUSTIVE, TUNE_LEARNED, TUNE_USER = 0, 1, 2, 3
+TUNE_DEFAULT, TUNE_EXHAUSTIVE, TUNE_LEARNED, TUNE_USER, TUNE_SAVED = 0, 1, 2, 3, 4
 LAYOUT_ABC, LAYOUT_CAB, LAYOUT_CBA = 0, 1, 2
 KERNEL_AUTO, KERNEL_WARP, KERNEL_TILE, KERNEL_GENERIC = 0, 1, 2, 3
 
@@ -45,7 +45,8 @@ EXPORTS = [
     "openfft_num_features", "openfft_candidate_features", "openfft_tune_times", "openfft_set_cost_model",
     "openfft_tc_gemm", "openfft_exec_r2c", "openfft_exec_c2r", "openfft_tc_debug", "openfft_set_host_chunks",
     "openfft_exec_c2c_host_async", "openfft_set_copy_streams",
-    "openfft_debug_alloc_fail", "openfft_checked_build", "openfft_debug_bounds_status", "openfft_nd_plan", "openfft_nd_exec", "openfft_nd_destroy", "openfft_nd_set_stream",
+    "openfft_debug_alloc_fail", "openfft_checked_build", "openfft_tuning_save", "openfft_tuning_load",
+    "openfft_tuning_lookup", "openfft_tuning_clear", "openfft_debug_bounds_status", "openfft_nd_plan", "openfft_nd_exec", "openfft_nd_destroy", "openfft_nd_set_stream",
     "openfft_nd_box", "openfft_nd_decomp_box", "openfft_nd_decomp_counts", "openfft_dist_rows", "openfft_dist_counts", "openfft_dist_pack_host", "openfft_dist_unpack_host",
     "openfft_dist_plan", "openfft_dist_destroy", "openfft_dist_set_stream", "openfft_dist_elem_bytes",
     "openfft_dist_exchange_counts", "openfft_dist_stage", "openfft_dist_pack", "openfft_dist_unpack",
@@ -128,6 +129,10 @@ def load():
             "openfft_tc_gemm": (i32, [i32, i32, i32, i32, i32, pf, pf, pf]),
             "openfft_debug_alloc_fail": (i32, [ctypes.c_longlong]),
             "openfft_checked_build": (i32, []),
+            "openfft_tuning_save": (i32, [ctypes.c_char_p]),
+            "openfft_tuning_load": (i32, [ctypes.c_char_p]),
+            "openfft_tuning_lookup": (i32, [i32, i32, i32, i32, i32, pi32, pi32]),
+            "openfft_tuning_clear": (i32, []),
             "openfft_debug_bounds_status": (i32, [pi32]),
             "openfft_nd_plan": (vp, [i32, pi32, i32, i32]),
             "openfft_nd_exec": (i32, [vp, vp, vp, i32]),
@@ -316,6 +321,29 @@ def openfft_exec_c2c_noalloc(Na: int, Nb: int, Nc: int, P: int, dtype: int, inp,
 def openfft_debug_alloc_fail(nth: int) -> None:
     """Test control: the nth device allocation from now on fails (0 = off)."""
     _check(load().openfft_debug_alloc_fail(nth))
+
+
+def openfft_tuning_save(path: str) -> None:
+    """Write the process-wide table of tuned choices to a text file."""
+    _check(load().openfft_tuning_save(os.fsencode(path)))
+
+
+def openfft_tuning_load(path: str) -> None:
+    """Merge a file of tuned choices into the process-wide table."""
+    _check(load().openfft_tuning_load(os.fsencode(path)))
+
+
+def openfft_tuning_lookup(Na: int, Nb: int, Nc: int, P: int, dtype: int):
+    """The recorded choice of a problem as (variant, arith, lines_per_cta,
+    kernel), or None."""
+    found = ctypes.c_int(0)
+    choice = (ctypes.c_int * 4)()
+    _check(load().openfft_tuning_lookup(Na, Nb, Nc, P, dtype, ctypes.byref(found), choice))
+    return tuple(int(v) for v in choice) if found.value else None
+
+
+def openfft_tuning_clear() -> None:
+    _check(load().openfft_tuning_clear())
 
 
 def openfft_checked_build() -> bool:
