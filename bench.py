@@ -288,10 +288,14 @@ def stage_roofline(of, torch, dev, n, chosen, phases, clocks):
     family, G_dom = dominant_kernel(chosen)
     traffic = profiled_traffic_scaled(stage_source_hash(), family, G_dom, n, N)
     arith_name = "ArDP" if all(c["arith"] == of.ARITH_DOUBLE_FLOAT for c in chosen.values()) else "ArF64"
+    if family == "warp" and arith_name == "ArDP" and n in (256, 512):
+        kname = "fft_warp_tma_kernel<%d, G=%d> (packed double-float, asynchronous output)" % (n, G_dom)
+    else:
+        kname = "fft_%s_kernel<%s, %d, G=%d>" % (family, arith_name, n, G_dom)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": "fft_%s_kernel<%s, %d, G=%d> (the tuned stage kernel of most plans; every stage "
-                          "launch of the step is one of the chosen stage kernels)" % (family, arith_name, n, G_dom),
+                "kernel": kname + " (the tuned stage kernel of most plans; every stage launch of the step is "
+                                  "one of the chosen stage kernels)",
                 "peak_kind": peak_kind,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_us": round(avg_s * 1e6, 2),
                 "share_of_step": round(fft_ms / max(1e-9, phases["exec"]["ms"]), 4)}
