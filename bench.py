@@ -31,6 +31,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -74,13 +75,22 @@ STAGE_SOURCES = ("fft_warp.cuh", "fft_warp_tma.cuh", "fft_tile.cuh", "stage_io.c
                  "fft_tma_512.cu")
 
 
+def source_code_only(text: str) -> str:
+    """A C/CUDA source with its comments removed and every run of white space
+    made one blank, so that editing a comment leaves the hash unchanged."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return re.sub(r"\s+", " ", text).strip()
+
+
 def stage_source_hash() -> str:
-    """Hash of the stage-kernel sources: a committed DRAM-traffic figure is only
-    reported while the kernel it was measured on is unchanged."""
+    """Hash of the code of the stage-kernel sources (comments and white space
+    aside): a committed DRAM-traffic figure is only reported while the kernel it
+    was measured on is unchanged."""
     h = hashlib.sha256()
     for f in STAGE_SOURCES:
-        with open(os.path.join(ROOT, "paper_1501_07350_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1501_07350_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(source_code_only(fh.read()).encode("utf-8"))
     return h.hexdigest()[:16]
 
 

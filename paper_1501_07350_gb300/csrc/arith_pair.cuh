@@ -2,10 +2,11 @@
 // real and imaginary lanes of every step in one packed FP32x2 instruction.
 //
 // sm_100 and later execute add / sub / mul / fma on .f32x2 operands: two IEEE
-// binary32 operations, each rounded to nearest, in one instruction.  The FP32
-// pipe does the same work per lane as with scalar instructions, but a packed
-// instruction takes one issue slot for two lanes, and the double-float stage
-// kernels are bound by instruction issue, not by the FP32 pipe.
+// binary32 operations, each rounded to nearest, in one instruction.  A packed
+// instruction takes one issue slot for two lanes and holds the FMA pipe for two
+// cycles, so the FP32 work per lane is that of scalar instructions at half the
+// issue slots.  With scalar instructions the double-float stage kernels were
+// bound by instruction issue; with packed ones the FMA pipe is their limit.
 //
 // Representation (ArDP): a complex value is C = {h, l}, h = (re.hi, im.hi) and
 // l = (re.lo, im.lo), each a 64-bit register pair -- the same 16 bytes, in the
@@ -18,8 +19,9 @@
 //
 // There is no packed negation: a twiddle product's rounding error
 // e = fma(a, b, -p) is formed as -e = fma(a, -b, p) with the negated factor
-// taken from the twiddle table and the sign folded into the next addition;
-// a scaling by a constant negates p by its sign bits.  Multiplication by -i swaps the lanes of a pair, which costs
+// among the twiddle's lane pairs (sign-bit flips of the table entry) and the
+// sign folded into the next addition; a scaling by a constant negates p by its
+// sign bits.  Multiplication by -i swaps the lanes of a pair, which costs
 // register moves, so the radix-4 and radix-8 butterflies fuse it into the
 // addition that consumes it (add_mi / sub_mi, lane signs through fma by
 // (+1, -1)).

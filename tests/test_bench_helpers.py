@@ -1,7 +1,8 @@
 """Host-side helpers of bench.py (no GPU).
 
 - roofline.traffic comes from a committed ncu summary only while the stage
-  kernel sources hash to the value recorded beside it;
+  kernel sources hash to the value recorded beside it; the hash covers the
+  code, not its comments or white space;
 - the dominant kernel is the (family, lines per CTA) most timed plans chose;
 - the FP32-issue roofline counts the double-float radix-pass arithmetic:
   16 operations per complex addition, 32 per twiddle product, radix 2 / 4 / 8
@@ -22,6 +23,23 @@ def test_profiled_traffic_follows_the_source_hash(tmp_path):
     assert bench.profiled_traffic("0" * 16, "warp", 8, 512, str(summary)) is None     # stale hash: no figure
     assert bench.profiled_traffic(h, "warp", 5, 512, str(summary)) is None            # no such capture
     assert bench.profiled_traffic(h, "warp", 8, 512, str(tmp_path / "absent.md")) is None
+
+
+def test_source_hash_ignores_comments_and_white_space():
+    a = "int f(int x) {  // twice x\n    return 2 * x; /* the\n  value */\n}\n"
+    b = "int f(int x) {\n  return 2 * x;\n}"
+    assert bench.source_code_only(a) == bench.source_code_only(b) == "int f(int x) { return 2 * x; }"
+    assert bench.source_code_only(a) != bench.source_code_only(b.replace("2", "3"))
+
+
+def test_profiled_traffic_of_the_committed_summaries():
+    for n in (256, 512):
+        path = os.path.join(os.path.dirname(bench.__file__), "profiles", "fft_warp_kernel_df_n%d.md" % n)
+        with open(path) as fh:
+            h = [ln.split(":", 1)[1].strip() for ln in fh if ln.strip().startswith("source_hash:")][0]
+        for G in (4, 8):
+            v = bench.profiled_traffic(h, "warp", G, n)
+            assert v is not None and 28.0 < v < 32.0, (n, G, v)     # about 2 x 16 bytes per point
 
 
 def test_dominant_kernel():
