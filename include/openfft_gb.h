@@ -109,7 +109,11 @@ enum {
  *   DOUBLE_FLOAT: each double is carried as an unevaluated sum of two floats
  *   and the butterflies use error-free transformations on the FP32 units
  *   (about 48 significant bits; finite inputs with |x| < 2^90 and outputs
- *   below 2^126).  Both meet the FP64 bound of 1e-12 relative L2. */
+ *   below 2^126).  Both meet the FP64 bound of 1e-12 relative L2.  The float
+ *   exponent range also bounds small values: on entry a component below
+ *   2^-103 in magnitude keeps only its leading 24 bits and one below 2^-126
+ *   becomes zero, so data whose magnitudes all lie that low should be scaled
+ *   first or transformed with NATIVE. */
 enum { OPENFFT_ARITH_NATIVE = 0, OPENFFT_ARITH_DOUBLE_FLOAT = 1 };
 /* Arithmetic of the split-precision plans (OPENFFT_C2C_SPLIT_TF32 / _BF16):
  * every axis n = R S (2 <= R, S <= 32) is transformed by two tensor-core
